@@ -1,0 +1,371 @@
+"""Benchmark: RK4 stepping of N coupled spin-torque oscillators on one B300.
+
+Workload (default): one reservoir of N = 10^4 oscillators, dense FP32
+Gaussian coupling W (std 0.1/sqrt(N), zero diagonal, 400 MB, larger than the
+126 MB L2 so it is re-read from HBM every stage), w_in ~ U[-1, 1],
+u ~ U[0, 1], random unit initial state, 100 RK4 substeps of 1e-11 s per input
+sample, states sampled every input sample; seed 0.  A "step" is one sto_run
+call over --ips input samples (one persistent kernel launch).  A second,
+smaller workload (N = 10^3, the same structure) is measured beside it.
+
+Metric: node-updates/s = N * RK4 steps / s (one node-update = one oscillator
+advanced by one full RK4 step, four stages).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+comparison arm; it runs a bounded sample of the same workload per step).
+Under torchrun with N > 1 processes every rank runs its own independent
+reservoir (replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 126 * 2 ** 20
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10000, help="oscillators of the main workload")
+    ap.add_argument("--ips", type=int, default=2, help="input samples per step")
+    ap.add_argument("--substeps", type=int, default=100)
+    ap.add_argument("--n-small", type=int, default=1000)
+    ap.add_argument("--ips-small", type=int, default=20)
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--grid", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(N, T, seed):
+    from paper_2312_01121_b300 import inputs
+    W = inputs.coupling_gaussian(N, seed=seed, dtype=np.float32)
+    w_in = inputs.f32(inputs.input_weights(N, 1, seed=seed))
+    m0 = inputs.f32(inputs.random_unit_states(N, seed=seed))
+    u = inputs.f32(inputs.input_series(T, 1, seed=seed))
+    return np.ascontiguousarray(W, dtype=np.float32), w_in, m0, u
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.out = out
+        else:
+            self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_device(N, args, ips, seed, torch, sto, dev):
+    """Device-resident timing of K steps; returns a dict of measurements."""
+    K, Wm = args.steps, args.warmup
+    T_all = (K + Wm) * ips
+    W, w_in, m0, u = workload(N, T_all, seed)
+    P = sto.Params(substeps=args.substeps)
+    stream = torch.cuda.current_stream()
+    Wd = torch.from_numpy(W).to(dev)
+    res = sto.Reservoir(Wd, torch.from_numpy(w_in).to(dev), P,
+                        m0=torch.from_numpy(m0).to(dev), stream=stream, grid=args.grid)
+    del Wd
+    torch.cuda.empty_cache()
+    info = res.info()
+    u_d = torch.from_numpy(u).to(dev)
+    st_d = torch.empty((ips, N), dtype=torch.float32, device=dev)
+    for i in range(Wm):
+        res.run(u_d[i * ips:(i + 1) * ips], st_d)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    rank, world, _ = dist_env()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev[0].record(stream)
+        for i in range(K):
+            j = Wm + i
+            res.run(u_d[j * ips:(j + 1) * ips], st_d)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    m = res.state()
+    finite = bool(np.all(np.isfinite(m)))
+    norm_err = float(np.max(np.abs(np.linalg.norm(m, axis=0) - 1.0)))
+    out = {"N": N, "ips": ips, "total_ms": total_ms, "per_launch_ms": per, "info": info,
+           "clocks": clk.summary(), "finite": finite, "norm_err": norm_err,
+           "node_updates": N * ips * args.substeps * K}
+    # end-to-end through the C ABI with host buffers (pinned), copies inside
+    if not args.no_e2e:
+        u_h = torch.from_numpy(u).pin_memory()
+        st_h = torch.empty((ips, N), dtype=torch.float32).pin_memory()
+        res.set_state(m0)
+        for i in range(Wm):
+            res.run(u_h[i * ips:(i + 1) * ips], st_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(K):
+            j = Wm + i
+            res.run(u_h[j * ips:(j + 1) * ips], st_h)
+        torch.cuda.synchronize()
+        out["e2e_s"] = time.perf_counter() - t0
+        out["h2d_bytes_per_step"] = ips * 1 * 4
+        out["d2h_bytes_per_step"] = ips * N * 4 + 16
+    res.close()
+    return out
+
+
+def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
+    """Node-updates/s of the FP64 oracle on a bounded sample of the workload."""
+    import oracle
+    W, w_in, m0, u = workload(N, 1, seed)
+    W64 = W.astype(np.float64)
+    del W
+    P = oracle.OracleParams(substeps=1)
+    m = m0.astype(np.float64)
+    t0 = time.perf_counter()
+    m, _ = oracle.run(P, W64, w_in.astype(np.float64), m, u.astype(np.float64), nthreads=nthreads)
+    one = time.perf_counter() - t0
+    steps = max(1, int(substeps_total_budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    uu = np.repeat(u.astype(np.float64), steps, axis=0)
+    m, _ = oracle.run(P, W64, w_in.astype(np.float64), m, uu, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": N * steps / dt, "steps": steps, "seconds": dt, "cores": nthreads}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle as the comparison arm, on this host's cores."""
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    N = args.n
+    nthreads = os.cpu_count() or 1
+    W, w_in, m0, u = workload(N, args.steps + args.warmup, 0)
+    W64 = W.astype(np.float64)
+    del W
+    P = oracle.OracleParams(substeps=1)
+    m = m0.astype(np.float64)
+    w64 = w_in.astype(np.float64)
+    u64 = u.astype(np.float64)
+    for i in range(args.warmup):
+        m, _ = oracle.run(P, W64, w64, m, u64[i:i + 1], nthreads=nthreads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = args.warmup + i
+        m, _ = oracle.run(P, W64, w64, m, u64[j:j + 1], nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = N * args.steps / dt
+    line = {"impl": "reference", "metric": "node-updates/s", "value": value,
+            "unit": "node-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"plain single reservoir N={N}, dense Gaussian FP32 W "
+                                   "(std 0.1/sqrt(N)); oracle step = 1 RK4 step (4 stages)",
+                       "N": N, "dt": 1e-11},
+            "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": nthreads,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} RK4 steps of N={N} (one per step)"},
+            "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2312_01121_b300 import build, sto
+    build.build()
+    sto.load_library()
+
+    main_r = time_device(args.n, args, args.ips, rank, torch, sto, dev)
+    small = None
+    if not args.no_small:
+        small = time_device(args.n_small, args, args.ips_small, rank, torch, sto, dev)
+
+    tot_ms = main_r["total_ms"]
+    updates = main_r["node_updates"]
+    e2e_s = main_r.get("e2e_s")
+    if world > 1:
+        t = torch.tensor([tot_ms, e2e_s or 0.0], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms, e2e_s = float(t[0]), float(t[1])
+        updates *= world
+    value = updates / (tot_ms / 1e3)
+
+    # roofline of the stepper: algorithmic bytes per launch / mean launch time
+    N, ips, S = args.n, args.ips, args.substeps
+    stages = 4 * S * ips
+    alg_bytes = stages * 4.0 * N * N + ips * 4.0 * N
+    mean_launch_s = statistics.mean(main_r["per_launch_ms"]) / 1e3
+    achieved = alg_bytes / mean_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = cpu_oracle_rate(N, args.cpu_seconds, 0, os.cpu_count() or 1)
+        except Exception as e:  # the baseline is informative, never fatal
+            cpu = {"error": str(e)}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": "node-updates/s",
+        "value": value,
+        "unit": "node-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "dtype_detail": "FP32 W and coupling matvec (FP32 accumulate); FP64 per-oscillator "
+                        "torque, RK4 combine and state",
+        "data": "synthetic",
+        "config": {
+            "workload": f"plain single reservoir, N={N}, dense Gaussian FP32 W (std 0.1/sqrt(N), "
+                        f"zero diagonal, {4 * N * N / 1e6:.0f} MB), u~U[0,1], RK4 dt=1e-11 s, "
+                        f"{S} substeps per input sample, states sampled every sample",
+            "N": N, "input_samples_per_step": ips, "rk4_steps_per_step": ips * S,
+            "stages_per_step": stages, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "W (400 MB) > L2 (126 MB): re-read from HBM every stage, no flush needed",
+            "plan": main_r["info"],
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "sto_persistent_kernel",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_launch_ms": mean_launch_s * 1e3,
+                     "us_per_stage": mean_launch_s * 1e6 / stages},
+        "clocks": main_r["clocks"],
+        "gpu_launches": args.steps,
+        "check": {"finite": main_r["finite"], "max_abs_norm_minus_1": main_r["norm_err"]},
+    }
+    if e2e_s:
+        line["e2e"] = {"value": updates / e2e_s, "unit": "node-updates/s",
+                       "h2d_bytes_per_step": main_r["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": main_r["d2h_bytes_per_step"]}
+    if cpu is not None:
+        if "value" in cpu:
+            line["cpu_baseline"] = {"value": cpu["value"], "unit": "node-updates/s",
+                                    "cores": cpu["cores"], "kind": "oracle",
+                                    "sample": f"{cpu['steps']} RK4 steps of the same N={N} "
+                                              f"workload in {cpu['seconds']:.1f} s "
+                                              "(FP64 C oracle, OpenMP over matvec rows)"}
+        else:
+            line["cpu_baseline"] = cpu
+    if small is not None:
+        Ns, ipss = args.n_small, args.ips_small
+        st = 4 * S * ipss
+        ml = statistics.mean(small["per_launch_ms"]) / 1e3
+        line["also"] = {
+            "workload": f"plain single reservoir, N={Ns}, dense Gaussian FP32 W (4 MB, "
+                        "on chip: latency-bound)",
+            "value": small["node_updates"] / (small["total_ms"] / 1e3),
+            "unit": "node-updates/s", "us_per_stage": ml * 1e6 / st,
+            "hbm_roofline_us_per_stage": 4.0 * Ns * Ns / (peak * 1e9) * 1e6,
+            "plan": small["info"], "clocks": small["clocks"],
+            "e2e_value": (small["node_updates"] / small["e2e_s"]) if small.get("e2e_s") else None,
+        }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * sto.h - C ABI of libsto, a B300 (sm_103a) simulator of N coupled
+ * spin-torque oscillators (STOs) used as a physical reservoir, after
+ * T. G. de Jong et al., "Virtual reservoir acceleration for CPU and GPU:
+ * case study for coupled spin-torque oscillator reservoir", arXiv 2312.01121.
+ *
+ * The method (Sec. 3.1, Eq. (gov)): every oscillator k carries a unit
+ * magnetisation m_k = (m^x, m^y, m^z) that follows the Landau-Lifshitz-Gilbert
+ * equation with spin-transfer torque
+ *     dm_k/dt = -gamma' m_k x b_k - alpha gamma' m_k x (m_k x b_k),
+ *     gamma'  = gamma / (1 + alpha^2),
+ *     b_k     = [H_appl + (H_K - 4 pi M) m_k^z] e_z              (Eq. gov)
+ *             + A_cp sum_i W[k,i] m_i^x e_x                      (Eq. coup)
+ *             + g A_in sum_j w_in[k,j] u_j e_x                   (Eq. in)
+ *             + H_s(m_k) p x m_k,
+ *     H_s(m)  = hbar eta I / (2 e (1 + lambda m.p) M V)           (Eq. gov).
+ * Eq. (coup) is printed with m_k^x inside the sum; the library reads it as
+ * m_i^x, the matrix-vector product W m^x that Sec. 3.3 describes.  Time
+ * stepping is classic RK4 with a fixed step dt (Sec. 3.2).  The input u is
+ * a discrete series (Sec. 3.1): sample t is held for `substeps` RK4 steps,
+ * after which the reservoir state (one component of every m_k, Sec. 3.1:
+ * "N-states are used as the nodes") is recorded.
+ *
+ * Units: fields in Oe, time in s, gamma in rad/(Oe s), M in emu/cm^3,
+ * V in cm^3, I in A, hbar in J s, e in C; H_s carries the factor 1e7 (J to
+ * erg) so that it comes out in Oe (134.87 Oe at the Table values).
+ *
+ * Precision: W and the coupling matrix-vector product are FP32 (FP32
+ * products, FP32 accumulation); the per-oscillator torque, the RK4 stage
+ * combination and the state are FP64.  Sampled states are returned in FP32.
+ *
+ * Conventions for every entry point:
+ *   - Return value: STO_OK (0) or a negative STO_E* code; sto_strerror()
+ *     describes it.  No call throws or aborts the process.  There is no CPU
+ *     fallback: without a usable CUDA device every compute call fails with
+ *     STO_ECUDA.
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the handle's device; the library
+ *     inspects them with cudaPointerGetAttributes.  Arrays are dense,
+ *     row-major, float32 unless stated otherwise.
+ *   - Arrays passed to sto_create are copied; the caller keeps ownership of
+ *     every pointer it passes and may free it once the call has returned.
+ *   - All device work is ordered on the stream given at creation.  Calls
+ *     that produce a status synchronise that stream before returning.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - After STO_ETIMEOUT or STO_ECUDA the handle's state is unspecified;
+ *     sto_set_state() makes it usable again.
+ */
+#ifndef STO_H_
+#define STO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STO_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define STO_API __attribute__((visibility("default")))
+#else
+#define STO_API
+#endif
+
+/* Status codes. */
+#define STO_OK 0
+#define STO_EINVAL (-1)      /* invalid argument (null pointer, size, range) */
+#define STO_ENOMEM (-2)      /* device or host allocation failed */
+#define STO_ECUDA (-3)       /* a CUDA runtime call failed (see sto_strerror) */
+#define STO_ETIMEOUT (-4)    /* a device-side wait exceeded its time limit */
+#define STO_ENONFINITE (-5)  /* NaN or Inf found in an input */
+#define STO_ENOTSUP (-6)     /* size or option outside what this build supports */
+
+/* Model parameters.  Defaults (sto_default_params) are Table "Summary of
+ * parameters" of Sec. 3.1 and the step of Sec. 3.2; substeps, n_in,
+ * input_gain and sample_component are not fixed by the paper. */
+typedef struct sto_params {
+  double gamma;       /* gyromagnetic ratio, rad/(Oe s)          1.764e7 */
+  double alpha;       /* Gilbert damping                          0.005 */
+  double Ms;          /* saturation magnetisation M, emu/cm^3     1448.3 */
+  double Hk;          /* anisotropy field H_K, Oe                 18616 */
+  double Happl;       /* applied field, Oe                        200 */
+  double eta;         /* spin polarisation                        0.537 */
+  double lambda;      /* spin-transfer torque asymmetry           0.288 */
+  double current;     /* I, A                                     2.5e-3 */
+  double volume;      /* V, cm^3                     pi*60^2*2 nm^3 */
+  double e_charge;    /* elementary charge, C             1.60217733e-19 */
+  double hbar;        /* reduced Planck constant, J s     1.05457266e-34 */
+  double p[3];        /* pinned-layer direction     (1, 0, 6.123234e-17) */
+  double A_cp;        /* coupling amplitude, Oe                   1 */
+  double A_in;        /* input amplitude, Oe                      1 */
+  double input_gain;  /* g, multiplies A_in                       1 */
+  double dt;          /* RK4 step, s                              1e-11 */
+  int32_t substeps;   /* RK4 steps per input sample (S)           100 */
+  int32_t n_in;       /* input channels N_in                      1 */
+  int32_t sample_component; /* recorded component: 0=x, 1=y, 2=z   0 */
+  int32_t reserved;   /* must be 0 */
+} sto_params;
+
+/* Launch-plan overrides for sto_create_ex.  Zero fields mean "choose". */
+typedef struct sto_config {
+  int32_t grid;        /* CTAs of the persistent kernel (1 .. #SMs, <= N) */
+  int32_t timeout_ms;  /* limit of every device-side wait (default 2000) */
+  int32_t reserved[6]; /* must be 0 */
+} sto_config;
+
+/* The launch plan chosen for a handle (read-only, for tuning and reports). */
+typedef struct sto_info {
+  int64_t N;
+  int32_t grid;          /* CTAs, one per SM, co-resident */
+  int32_t rows_max;      /* most oscillators owned by one CTA */
+  int32_t panel_cols;    /* columns of W per streamed panel */
+  int32_t panels;        /* panels per row block (ceil(N / panel_cols)) */
+  int32_t ring_slots;    /* shared-memory panel buffers per CTA */
+  int32_t resident;      /* 1: each CTA keeps its rows of W on chip */
+  int32_t smem_bytes;    /* dynamic shared memory per CTA */
+  int32_t sm_count;      /* SMs of the device */
+  int64_t w_bytes;       /* bytes of W streamed per RK4 stage (4 N^2) */
+} sto_info;
+
+typedef struct sto_handle sto_handle; /* opaque */
+
+/* Fill *out with the defaults above.  Never fails. */
+STO_API void sto_default_params(sto_params* out);
+
+/* Create a simulator for one reservoir of N oscillators (Sec. 3.1).
+ *   N       >= 1.  The largest N is set by shared memory: about 21000 with
+ *           148 CTAs on a B300 (STO_ENOTSUP beyond).
+ *   params  model parameters; checked for finiteness and ranges.
+ *   W       N x N coupling matrix, row k = target oscillator, column i =
+ *           source (Eq. coup), host or device.  The paper's W has a zero
+ *           diagonal; any finite matrix is accepted.
+ *   w_in    N x n_in input weights (Eq. in), host or device.
+ *   m0      initial state, 3 x N (all m^x, then m^y, then m^z), host or
+ *           device; NULL selects Eq. (initial): every m_k =
+ *           (sin phi0 cos phi0, sin phi0 sin phi0, cos phi0), phi0 = 2pi/360.
+ *   stream  cudaStream_t to order all work on (NULL = legacy default).
+ *   out     receives the handle; *out is NULL on failure.
+ * Errors: STO_EINVAL, STO_ENONFINITE (NaN/Inf in W, w_in or m0),
+ *         STO_ENOMEM, STO_ENOTSUP, STO_ECUDA. */
+STO_API int sto_create(int64_t N, const sto_params* params, const float* W,
+               const float* w_in, const float* m0, void* stream,
+               sto_handle** out);
+
+/* sto_create with launch-plan overrides (cfg may be NULL). */
+STO_API int sto_create_ex(int64_t N, const sto_params* params, const float* W,
+                  const float* w_in, const float* m0, void* stream,
+                  const sto_config* cfg, sto_handle** out);
+
+/* Replace the model parameters (not N, n_in or the plan).  Lets a caller
+ * sweep I, A_cp, the gain, dt, substeps ... without re-uploading W.
+ * n_in must equal the value given at creation.  Errors: STO_EINVAL. */
+STO_API int sto_set_params(sto_handle* h, const sto_params* params);
+
+/* Set / read the state, 3 x N float32 (m^x block, m^y block, m^z block),
+ * host or device.  The internal state is FP64; sto_get_state rounds it. */
+STO_API int sto_set_state(sto_handle* h, const float* m);
+STO_API int sto_get_state(const sto_handle* h, float* m);
+/* Exact FP64 state, 3 x N doubles, host or device (checkpoint / resume). */
+STO_API int sto_set_state_f64(sto_handle* h, const double* m);
+STO_API int sto_get_state_f64(const sto_handle* h, double* m);
+
+/* Advance the reservoir over T input samples (Sec. 3.1, Sec. 3.2).
+ *   u           T x n_in float32 input series, host or device (may be NULL
+ *               only if T == 0).
+ *   T           >= 0; T == 0 returns STO_OK and does nothing.
+ *   states_out  T x N float32, host or device, or NULL: after sample t,
+ *               states_out[t*N + k] = component `sample_component` of m_k.
+ * For every sample t: the input field of Eq. (in) is formed from u[t] and
+ * held for `substeps` classic RK4 steps of size dt, each stage evaluating
+ * the full coupling field A_cp W m^x of Eq. (coup).  The state advances in
+ * place.  The whole call is one persistent kernel launch; it synchronises
+ * the stream once at the end to read the device error word.
+ * Errors: STO_EINVAL, STO_ETIMEOUT, STO_ECUDA, STO_ENOMEM (host buffers
+ *         larger than any earlier call need a device staging buffer). */
+STO_API int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out);
+
+/* Report the launch plan. */
+STO_API int sto_get_info(const sto_handle* h, sto_info* out);
+
+/* Release all device memory of the handle (NULL is allowed). */
+STO_API void sto_destroy(sto_handle* h);
+
+/* Text for a status code, including the CUDA error text of the most recent
+ * STO_ECUDA on the calling thread.  The pointer stays valid until the next
+ * call on that thread. */
+STO_API const char* sto_strerror(int code);
+
+/* STO_ABI_VERSION of the built library. */
+STO_API int sto_abi_version(void);
+
+/* Fault injection for tests of the device-side timeouts.  With cta >= 0,
+ * the next sto_run on h makes CTA `cta` never publish its oscillators, so
+ * every other CTA's wait for them runs into the timeout and the call returns
+ * STO_ETIMEOUT with the handle still usable after sto_set_state.  cta < 0
+ * clears it.  Only meaningful when the plan has more than one CTA. */
+STO_API int sto_debug_inject_stall(sto_handle* h, int32_t cta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STO_H_ */

@@ -1,0 +1,566 @@
+// libsto host side: the C ABI declared in include/sto.h.
+//
+// The handle owns, in device memory of the device current at creation:
+//   W in the tiled layout of the plan (N x P*128 floats, zero padded),
+//   w_in (N x n_in floats), the FP64 state (3 x N doubles),
+//   the tagged m^x exchange buffer (2 x N 64-bit words), the error word,
+//   and staging buffers for calls made with host pointers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sto.h"
+#include "sto_kernel.cuh"
+
+namespace {
+
+thread_local char g_errbuf[512];
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+constexpr int kDefaultTimeoutMs = 2000;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = e;
+  return STO_ECUDA;
+}
+
+#define STO_CUDA(call)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Plan {
+  int G = 1, R_max = 1, P = 1, ns = 1, resident = 1, rpw = 1;
+  size_t smem = 0;
+};
+
+// Dynamic shared memory of the stepper for a plan with `ns` ring slots.
+size_t smem_bytes(int R_max, int P, int ns) {
+  size_t b = static_cast<size_t>(ns) * R_max * sto::kPanelCols * 4;  // ring
+  b += static_cast<size_t>(P) * sto::kPanelCols * 4;                 // xs
+  b += static_cast<size_t>((R_max + 3) & ~3) * 4;                    // hs
+  b += static_cast<size_t>(2 * ns) * 8 + 16;                         // barriers, abort flag
+  return b;
+}
+
+// Choose the CTA count, panel ring and residency for N oscillators.
+int make_plan(int64_t N, int grid_req, int sm_count, size_t smem_max, Plan* out) {
+  Plan p;
+  p.P = static_cast<int>((N + sto::kPanelCols - 1) / sto::kPanelCols);
+  auto fill = [&](int G) -> bool {
+    p.G = G;
+    p.R_max = static_cast<int>((N + G - 1) / G);
+    if (p.R_max > sto::kConsWarps * sto::kMaxRowsPerWarp) return false;
+    p.rpw = (p.R_max + sto::kConsWarps - 1) / sto::kConsWarps;
+    if (smem_bytes(p.R_max, p.P, p.P) <= smem_max) {
+      p.resident = 1;
+      p.ns = p.P;
+    } else {
+      p.resident = 0;
+      const size_t fixed = smem_bytes(p.R_max, p.P, 0);
+      const size_t per = static_cast<size_t>(p.R_max) * sto::kPanelCols * 4 + 16;
+      if (fixed >= smem_max) return false;
+      p.ns = static_cast<int>((smem_max - fixed) / per);
+      if (p.ns > 8) p.ns = 8;
+      if (p.ns < 2) return false;
+    }
+    p.smem = smem_bytes(p.R_max, p.P, p.ns);
+    return p.smem <= smem_max;
+  };
+  if (grid_req > 0) {
+    if (grid_req > sm_count || grid_req > N) return STO_EINVAL;
+    if (!fill(grid_req)) return STO_ENOTSUP;
+  } else if (fill(1) && p.resident) {
+    // the whole W fits in one CTA: no inter-CTA exchange at all
+  } else {
+    const int G = static_cast<int>(N < sm_count ? N : sm_count);
+    if (!fill(G)) return STO_ENOTSUP;
+  }
+  *out = p;
+  return STO_OK;
+}
+
+void default_params(sto_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->gamma = 1.764e7;
+  p->alpha = 0.005;
+  p->Ms = 1448.3;
+  p->Hk = 18616.0;
+  p->Happl = 200.0;
+  p->eta = 0.537;
+  p->lambda = 0.288;
+  p->current = 2.5e-3;
+  p->volume = M_PI * 60.0 * 60.0 * 2.0 * 1e-21;  // pi 60^2 2 nm^3 in cm^3
+  p->e_charge = 1.60217733e-19;
+  p->hbar = 1.05457266e-34;
+  p->p[0] = 1.0;
+  p->p[1] = 0.0;
+  p->p[2] = 6.123234e-17;
+  p->A_cp = 1.0;
+  p->A_in = 1.0;
+  p->input_gain = 1.0;
+  p->dt = 1e-11;
+  p->substeps = 100;
+  p->n_in = 1;
+  p->sample_component = 0;
+}
+
+int check_params(const sto_params* p) {
+  if (!p) return STO_EINVAL;
+  const double v[] = {p->gamma, p->alpha, p->Ms, p->Hk, p->Happl, p->eta, p->lambda,
+                      p->current, p->volume, p->e_charge, p->hbar, p->p[0], p->p[1],
+                      p->p[2], p->A_cp, p->A_in, p->input_gain, p->dt};
+  for (double x : v)
+    if (!std::isfinite(x)) return STO_EINVAL;
+  if (p->Ms <= 0 || p->volume <= 0 || p->e_charge <= 0 || p->dt <= 0) return STO_EINVAL;
+  if (p->substeps < 1 || p->n_in < 1 || p->n_in > 4096) return STO_EINVAL;
+  if (p->sample_component < 0 || p->sample_component > 2 || p->reserved != 0) return STO_EINVAL;
+  return STO_OK;
+}
+
+}  // namespace
+
+struct sto_handle {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  int64_t N = 0;
+  sto_params params{};
+  Plan plan;
+  int timeout_ms = kDefaultTimeoutMs;
+  int inject_cta = -1;
+  uint64_t stage_counter = 0;
+  float* d_W = nullptr;
+  float* d_win = nullptr;
+  double* d_state = nullptr;
+  unsigned long long* d_xbuf = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;  // pinned, 4 ints
+  float* d_u = nullptr;
+  size_t d_u_cap = 0;
+  float* d_states = nullptr;
+  size_t d_states_cap = 0;
+};
+
+namespace {
+
+void free_handle(sto_handle* h) {
+  if (!h) return;
+  cudaFree(h->d_W);
+  cudaFree(h->d_win);
+  cudaFree(h->d_state);
+  cudaFree(h->d_xbuf);
+  cudaFree(h->d_err);
+  cudaFree(h->d_u);
+  cudaFree(h->d_states);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  delete h;
+}
+
+template <int RPW>
+cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(pl.smem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.G);
+  cfg.blockDim = dim3(sto::kThreads);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident, or the launch fails
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW>, a);
+}
+
+cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  if (pl.rpw <= 1) return launch_rpw<1>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8>(pl, a, s);
+  return launch_rpw<16>(pl, a, s);
+}
+
+// Device copy of n floats from a host or device pointer into dst.
+int upload_floats(float* dst, const float* src, size_t n, cudaStream_t s) {
+  STO_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float),
+                           is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return STO_OK;
+}
+
+// n floats from host or device into a host vector.
+int fetch_floats(std::vector<float>* out, const float* src, size_t n, cudaStream_t s) {
+  out->resize(n);
+  STO_CUDA(cudaMemcpyAsync(out->data(), src, n * sizeof(float), cudaMemcpyDefault, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  return STO_OK;
+}
+
+int any_nonfinite(const float* d_p, long long n, cudaStream_t s, int* d_flag, int* h_flag,
+                  bool* result) {
+  STO_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  if (n > 0) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    sto::nonfinite_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(d_p, n, d_flag);
+    STO_CUDA(cudaGetLastError());
+  }
+  STO_CUDA(cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  *result = (*h_flag != 0);
+  return STO_OK;
+}
+
+int set_state_host_f64(sto_handle* h, const double* m) {
+  const size_t n = 3 * static_cast<size_t>(h->N);
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(m[i])) return STO_ENONFINITE;
+  STO_CUDA(cudaMemcpyAsync(h->d_state, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return STO_OK;
+}
+
+int grow(float** buf, size_t* cap, size_t n) {
+  if (*cap >= n) return STO_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, n * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return STO_ENOMEM;
+  }
+  *cap = n;
+  return STO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sto_default_params(sto_params* out) {
+  if (out) default_params(out);
+}
+
+int sto_abi_version(void) { return STO_ABI_VERSION; }
+
+const char* sto_strerror(int code) {
+  const char* base = "unknown status";
+  switch (code) {
+    case STO_OK: base = "ok"; break;
+    case STO_EINVAL: base = "invalid argument"; break;
+    case STO_ENOMEM: base = "out of memory"; break;
+    case STO_ECUDA: base = "CUDA error"; break;
+    case STO_ETIMEOUT: base = "device wait timed out"; break;
+    case STO_ENONFINITE: base = "non-finite input"; break;
+    case STO_ENOTSUP: base = "not supported by this build"; break;
+    default: break;
+  }
+  if (code == STO_ECUDA && g_last_cuda != cudaSuccess)
+    std::snprintf(g_errbuf, sizeof(g_errbuf), "%s: %s (%s)", base, cudaGetErrorName(g_last_cuda),
+                  cudaGetErrorString(g_last_cuda));
+  else
+    std::snprintf(g_errbuf, sizeof(g_errbuf), "%s", base);
+  return g_errbuf;
+}
+
+int sto_create(int64_t N, const sto_params* params, const float* W, const float* w_in,
+               const float* m0, void* stream, sto_handle** out) {
+  return sto_create_ex(N, params, W, w_in, m0, stream, nullptr, out);
+}
+
+int sto_create_ex(int64_t N, const sto_params* params, const float* W, const float* w_in,
+                  const float* m0, void* stream, const sto_config* cfg, sto_handle** out) {
+  if (!out) return STO_EINVAL;
+  *out = nullptr;
+  if (N < 1 || !W || !w_in) return STO_EINVAL;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (cfg) {
+    if (cfg->grid < 0 || cfg->timeout_ms < 0) return STO_EINVAL;
+    for (int i = 0; i < 6; ++i)
+      if (cfg->reserved[i] != 0) return STO_EINVAL;
+  }
+  if (N > (1LL << 20)) return STO_ENOTSUP;
+
+  sto_handle* h = new (std::nothrow) sto_handle();
+  if (!h) return STO_ENOMEM;
+  h->N = N;
+  h->params = *params;
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (cfg && cfg->timeout_ms > 0) h->timeout_ms = cfg->timeout_ms;
+
+  auto fail = [&](int code) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  int smem_optin = 0;
+  if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
+          cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                  h->device)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  rc = make_plan(N, cfg ? cfg->grid : 0, h->sm_count, static_cast<size_t>(smem_optin), &h->plan);
+  if (rc) return fail(rc);
+
+  const int n_in = params->n_in;
+  const size_t wt_elems = static_cast<size_t>(N) * h->plan.P * sto::kPanelCols;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  if (!alloc(reinterpret_cast<void**>(&h->d_W), wt_elems * 4) ||
+      !alloc(reinterpret_cast<void**>(&h->d_win), static_cast<size_t>(N) * n_in * 4) ||
+      !alloc(reinterpret_cast<void**>(&h->d_state), 3 * static_cast<size_t>(N) * 8) ||
+      !alloc(reinterpret_cast<void**>(&h->d_xbuf), 2 * static_cast<size_t>(N) * 8) ||
+      !alloc(reinterpret_cast<void**>(&h->d_err), 16))
+    return fail(STO_ENOMEM);
+  if (cudaMallocHost(reinterpret_cast<void**>(&h->h_err), 16) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_err = nullptr;
+    return fail(STO_ENOMEM);
+  }
+  cudaStream_t s = h->stream;
+
+  // W: stage row-major on the device, check, tile.
+  const float* d_src = W;
+  float* d_tmp = nullptr;
+  if (!is_device_ptr(W)) {
+    if (!alloc(reinterpret_cast<void**>(&d_tmp), static_cast<size_t>(N) * N * 4))
+      return fail(STO_ENOMEM);
+    e = cudaMemcpyAsync(d_tmp, W, static_cast<size_t>(N) * N * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFree(d_tmp); return fail(cuda_fail(e)); }
+    d_src = d_tmp;
+  }
+  bool bad = false;
+  rc = any_nonfinite(d_src, N * N, s, h->d_err, h->h_err, &bad);
+  if (!rc && bad) rc = STO_ENONFINITE;
+  if (!rc) {
+    e = cudaMemsetAsync(h->d_W, 0, wt_elems * 4, s);
+    if (e == cudaSuccess) {
+      long long blocks = (N * N + 255) / 256;
+      if (blocks > 8192) blocks = 8192;
+      sto::tile_w_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+          d_src, h->d_W, static_cast<int>(N), h->plan.G, h->plan.P);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (d_tmp) cudaFree(d_tmp);
+  if (rc) return fail(rc);
+
+  // w_in
+  rc = upload_floats(h->d_win, w_in, static_cast<size_t>(N) * n_in, s);
+  if (!rc) {
+    rc = any_nonfinite(h->d_win, N * n_in, s, h->d_err, h->h_err, &bad);
+    if (!rc && bad) rc = STO_ENONFINITE;
+  }
+  if (rc) return fail(rc);
+
+  // exchange buffer: tag 0xffffffff is never used by a launch
+  e = cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(N) * 8, s);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+
+  // state
+  std::vector<double> m(3 * static_cast<size_t>(N));
+  if (m0) {
+    std::vector<float> mf;
+    rc = fetch_floats(&mf, m0, m.size(), s);
+    if (rc) return fail(rc);
+    for (size_t i = 0; i < m.size(); ++i) m[i] = mf[i];
+  } else {
+    const double phi0 = 2.0 * M_PI / 360.0;  // Eq. (initial)
+    for (int64_t k = 0; k < N; ++k) {
+      m[k] = std::sin(phi0) * std::cos(phi0);
+      m[N + k] = std::sin(phi0) * std::sin(phi0);
+      m[2 * N + k] = std::cos(phi0);
+    }
+  }
+  rc = set_state_host_f64(h, m.data());
+  if (rc) return fail(rc);
+  *out = h;
+  return STO_OK;
+}
+
+void sto_destroy(sto_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+}
+
+int sto_set_params(sto_handle* h, const sto_params* params) {
+  if (!h) return STO_EINVAL;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (params->n_in != h->params.n_in) return STO_EINVAL;
+  h->params = *params;
+  return STO_OK;
+}
+
+int sto_get_info(const sto_handle* h, sto_info* out) {
+  if (!h || !out) return STO_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->N = h->N;
+  out->grid = h->plan.G;
+  out->rows_max = h->plan.R_max;
+  out->panel_cols = sto::kPanelCols;
+  out->panels = h->plan.P;
+  out->ring_slots = h->plan.ns;
+  out->resident = h->plan.resident;
+  out->smem_bytes = static_cast<int32_t>(h->plan.smem);
+  out->sm_count = h->sm_count;
+  out->w_bytes = 4 * h->N * h->N;
+  return STO_OK;
+}
+
+int sto_set_state(sto_handle* h, const float* m) {
+  if (!h || !m) return STO_EINVAL;
+  std::vector<float> mf;
+  int rc = fetch_floats(&mf, m, 3 * static_cast<size_t>(h->N), h->stream);
+  if (rc) return rc;
+  std::vector<double> md(mf.begin(), mf.end());
+  return set_state_host_f64(h, md.data());
+}
+
+int sto_set_state_f64(sto_handle* h, const double* m) {
+  if (!h || !m) return STO_EINVAL;
+  const size_t n = 3 * static_cast<size_t>(h->N);
+  std::vector<double> md(n);
+  STO_CUDA(cudaMemcpyAsync(md.data(), m, n * sizeof(double), cudaMemcpyDefault, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return set_state_host_f64(h, md.data());
+}
+
+int sto_get_state_f64(const sto_handle* h, double* m) {
+  if (!h || !m) return STO_EINVAL;
+  STO_CUDA(cudaMemcpyAsync(m, h->d_state, 3 * static_cast<size_t>(h->N) * sizeof(double),
+                           cudaMemcpyDefault, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return STO_OK;
+}
+
+int sto_get_state(const sto_handle* h, float* m) {
+  if (!h || !m) return STO_EINVAL;
+  const size_t n = 3 * static_cast<size_t>(h->N);
+  std::vector<double> md(n);
+  STO_CUDA(cudaMemcpyAsync(md.data(), h->d_state, n * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  std::vector<float> mf(n);
+  for (size_t i = 0; i < n; ++i) mf[i] = static_cast<float>(md[i]);
+  STO_CUDA(cudaMemcpyAsync(m, mf.data(), n * sizeof(float), cudaMemcpyDefault, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return STO_OK;
+}
+
+int sto_debug_inject_stall(sto_handle* h, int32_t cta) {
+  if (!h) return STO_EINVAL;
+  h->inject_cta = cta < 0 ? -1 : cta;
+  return STO_OK;
+}
+
+int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
+  if (!h || T < 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  if (!u) return STO_EINVAL;
+  const sto_params& P = h->params;
+  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
+  const int64_t N = h->N;
+  cudaStream_t s = h->stream;
+  const size_t n_u = static_cast<size_t>(T) * P.n_in;
+  const size_t n_states = static_cast<size_t>(T) * N;
+
+  const float* d_u = u;
+  if (!is_device_ptr(u)) {
+    int rc = grow(&h->d_u, &h->d_u_cap, n_u);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(h->d_u, u, n_u * 4, cudaMemcpyHostToDevice, s));
+    d_u = h->d_u;
+  }
+  float* d_states = states_out;
+  const bool host_states = states_out && !is_device_ptr(states_out);
+  if (host_states) {
+    int rc = grow(&h->d_states, &h->d_states_cap, n_states);
+    if (rc) return rc;
+    d_states = h->d_states;
+  }
+
+  // tags [base, base + stages] are fresh: none was written before
+  if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
+    STO_CUDA(cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(N) * 8, s));
+    h->stage_counter = 0;
+  }
+  const uint64_t base = h->stage_counter + 1;
+  h->stage_counter = base + stages;
+
+  sto::KArgs a{};
+  a.W = h->d_W;
+  a.w_in = h->d_win;
+  a.u = d_u;
+  a.state = h->d_state;
+  a.states_out = d_states;
+  a.xbuf = h->d_xbuf;
+  a.err = h->d_err;
+  a.N = static_cast<int>(N);
+  a.n_in = P.n_in;
+  a.T = static_cast<int>(T);
+  a.S = P.substeps;
+  a.P = h->plan.P;
+  a.ns = h->plan.ns;
+  a.resident = h->plan.resident;
+  a.comp = P.sample_component;
+  a.inject_cta = h->inject_cta;
+  a.tag_base = static_cast<unsigned>(base);
+  a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
+  const double gp = P.gamma / (1.0 + P.alpha * P.alpha);
+  a.gdt = -gp * P.dt;
+  a.alpha = P.alpha;
+  a.happl = P.Happl;
+  a.hkp = P.Hk - 4.0 * M_PI * P.Ms;
+  a.hs0 = P.hbar * P.eta * P.current * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume);
+  a.lambda = P.lambda;
+  a.px = P.p[0];
+  a.py = P.p[1];
+  a.pz = P.p[2];
+  a.acp = P.A_cp;
+  a.ain_g = P.A_in * P.input_gain;
+
+  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
+  STO_CUDA(launch_stepper(h->plan, a, s));
+  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s));
+  if (host_states)
+    STO_CUDA(cudaMemcpyAsync(states_out, d_states, n_states * 4, cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  h->inject_cta = -1;
+  if (h->h_err[0] != 0) return h->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  return STO_OK;
+}
+
+}  // extern "C"

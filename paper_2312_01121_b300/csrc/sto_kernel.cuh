@@ -1,0 +1,501 @@
+// Device code of libsto: the persistent RK4 stepper for N coupled
+// spin-torque oscillators (arXiv 2312.01121, Sec. 3.1 Eq. (gov), Sec. 3.2).
+//
+// One cooperative launch runs a whole sto_run call.  CTA c owns oscillators
+// [r0, r0 + R) and the matching rows of W.  Per RK4 stage every CTA
+//   1. gathers the stage's m^x of all N oscillators into shared memory
+//      (tagged 8-byte words published by their owners, see below),
+//   2. computes h_k = sum_i W[k,i] m^x_i for its rows while a producer warp
+//      streams its W rows through a shared-memory ring with TMA bulk copies,
+//   3. evaluates the LLG + spin-transfer torque of its oscillators in FP64,
+//      combines the RK4 stage and publishes the next stage's m^x.
+// The W stream never waits for step 1: W is constant, so the producer runs
+// ahead across stage boundaries and HBM stays busy while CTAs synchronise.
+//
+// Inter-CTA exchange: the m^x of oscillator k for stage tag g is the 64-bit
+// word (tag << 32 | float bits) at xbuf[(g & 1) * N + k], written with one
+// st.relaxed.gpu and read with ld.relaxed.gpu.  A reader accepts a word only
+// when its tag equals g, so no grid barrier and no fence is needed; the two
+// parity buffers are safe because a CTA can only publish tag g + 1 after it
+// has read every tag-g word, which every owner wrote after reading all of
+// its tag g - 1 words.
+//
+// Every wait is bounded by a_.timeout_ns of %globaltimer; on expiry the kernel
+// records STO_ETIMEOUT in the error word; the consumer warps of a CTA agree
+// on leaving through an OR-reducing barrier (bar.red.or), and the producer
+// warp waits for its copies in flight before it leaves.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sto {
+
+constexpr int kPanelCols = 128;                 // W columns per panel: 1 float4 per lane
+constexpr int kConsWarps = 16;                  // warps that consume panels
+constexpr int kCons = kConsWarps * 32;          // consumer threads
+constexpr int kThreads = kCons + 32;            // + one producer warp
+constexpr int kMaxRowsPerWarp = 16;             // rows of a CTA <= 256
+
+// Error word layout (int32[4]): code, CTA, stage tag, site.
+enum ErrSite { kSiteGather = 1, kSiteFull = 2, kSiteEmpty = 3, kSiteDrain = 4 };
+constexpr int kErrTimeout = -4;  // == STO_ETIMEOUT
+
+struct KArgs {
+  const float* W;            // tiled row blocks (see host planner)
+  const float* w_in;         // N x n_in
+  const float* u;            // T x n_in
+  double* state;             // 3 x N: m^x | m^y | m^z
+  float* states_out;         // T x N or nullptr
+  unsigned long long* xbuf;  // 2 x N tagged words
+  int* err;                  // int32[4]
+  int N, n_in, T, S, P, ns, resident, comp, inject_cta;
+  unsigned int tag_base;
+  unsigned long long timeout_ns;
+  // FP64 constants of Eq. (gov)
+  double gdt;    // -gamma' * dt
+  double alpha, happl, hkp, hs0, lambda, px, py, pz, acp, ain_g;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over the consumer warps that also ORs `flag` across them, so every
+// consumer takes the same abort decision.
+__device__ __forceinline__ bool consumer_sync_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(flag)), "n"(kCons)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ unsigned long long pack_x(float x, unsigned tag) {
+  return (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(x);
+}
+
+__device__ __noinline__ void report_error(int* err, int code, int cta, unsigned tag, int site) {
+  if (atomicCAS(err, 0, code) == 0) {
+    err[1] = cta;
+    err[2] = static_cast<int>(tag);
+    err[3] = site;
+  }
+}
+
+// Wait for an mbarrier phase; false after timeout or when the CTA aborts.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long timeout_ns,
+                                                  const volatile int* s_abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t n = 1;; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 15u) == 0) {
+      if (s_abort && *s_abort) return false;
+      if (gtimer() - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+// Spin on one tagged word until it carries `tag`; false on timeout or when
+// any CTA has recorded an error.
+__device__ __noinline__ bool poll_word(const unsigned long long* p, unsigned tag,
+                                       const KArgs& a, unsigned long long* out) {
+  const unsigned long long t0 = gtimer();
+  for (uint32_t n = 1;; ++n) {
+    unsigned long long w = ld_relaxed_u64(p);
+    if (static_cast<unsigned>(w >> 32) == tag) {
+      *out = w;
+      return true;
+    }
+    if ((n & 31u) == 0) {
+      if (ld_relaxed_i32(a.err) != 0) return false;
+      if (gtimer() - t0 > a.timeout_ns) {
+        report_error(a.err, kErrTimeout, blockIdx.x, tag, kSiteGather);
+        return false;
+      }
+    }
+  }
+}
+
+// Copy the stage's m^x (tag) of all N oscillators into xs.
+__device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag, int ctid) {
+  const unsigned long long* xb = a.xbuf + static_cast<size_t>(tag & 1u) * a.N;
+  for (int base = ctid; base < a.N; base += 4 * kCons) {
+    unsigned long long w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = base + q * kCons;
+      w[q] = (i < a.N) ? ld_relaxed_u64(xb + i) : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = base + q * kCons;
+      if (i < a.N) {
+        if (static_cast<unsigned>(w[q] >> 32) != tag && !poll_word(xb + i, tag, a, &w[q]))
+          return false;
+        xs[i] = __uint_as_float(static_cast<unsigned>(w[q]));
+      }
+    }
+  }
+  return true;
+}
+
+// dt * dm/dt of Eq. (gov) for one oscillator, in FP64.
+// hx = coupling + input field along e_x (Eq. coup + Eq. in).
+__device__ __forceinline__ void llg_increment(const KArgs& a, double mx, double my, double mz,
+                                              double hx, double& dx, double& dy, double& dz) {
+  const double s = mx * a.px + my * a.py + mz * a.pz;        // m . p
+  const double hs = a.hs0 / (1.0 + a.lambda * s);            // H_s(m)
+  const double cx = a.py * mz - a.pz * my;                   // p x m
+  const double cy = a.pz * mx - a.px * mz;
+  const double cz = a.px * my - a.py * mx;
+  const double bx = hx + hs * cx;                            // b
+  const double by = hs * cy;
+  const double bz = a.happl + a.hkp * mz + hs * cz;
+  const double tx = my * bz - mz * by;                       // m x b
+  const double ty = mz * bx - mx * bz;
+  const double tz = mx * by - my * bx;
+  const double ux = my * tz - mz * ty;                       // m x (m x b)
+  const double uy = mz * tx - mx * tz;
+  const double uz = mx * ty - my * tx;
+  dx = a.gdt * (tx + a.alpha * ux);                          // -gamma' dt (...)
+  dy = a.gdt * (ty + a.alpha * uy);
+  dz = a.gdt * (tz + a.alpha * uz);
+}
+
+// ------------------------------------------------------------ the stepper
+
+template <int RPW>
+__global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int c = blockIdx.x;
+  const int G = gridDim.x;
+  const int q = a.N / G, rem = a.N % G;
+  const int R = q + (c < rem ? 1 : 0);
+  const int r0 = c * q + (c < rem ? c : rem);
+  const int R_max = q + (rem > 0 ? 1 : 0);
+  const size_t slot_floats = static_cast<size_t>(R_max) * kPanelCols;
+
+  float* ring = reinterpret_cast<float*>(smem);
+  float* xs = ring + slot_floats * a.ns;
+  float* hs = xs + static_cast<size_t>(a.P) * kPanelCols;
+  uint64_t* full = reinterpret_cast<uint64_t*>(hs + ((R_max + 3) & ~3));
+  uint64_t* empty = full + a.ns;
+  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + a.ns);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < a.ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsWarps);
+    }
+    *s_abort = 0;
+    fence_mbar_init();
+  }
+  for (int i = tid; i < a.P * kPanelCols; i += kThreads) xs[i] = 0.f;
+  __syncthreads();
+
+  const float* Wc = a.W + static_cast<size_t>(r0) * a.P * kPanelCols;
+  const uint32_t panel_bytes = static_cast<uint32_t>(R) * kPanelCols * 4u;
+
+  // ------------------------------------------------------------ producer
+  if (warp == kConsWarps) {
+    if (lane == 0) {
+      const uint64_t pol = a.resident ? policy_evict_last() : policy_evict_first();
+      const long long total =
+          a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
+      long long it = 0;
+      int slot = 0, j = 0;
+      uint32_t lap = 0;  // it / ns
+      bool ok = true;
+      for (; it < total; ++it) {
+        if (!a.resident && lap > 0) {
+          if (!mbar_wait_bounded(&empty[slot], (lap - 1u) & 1u, a.timeout_ns, s_abort)) {
+            ok = false;
+            break;
+          }
+        }
+        mbar_arrive_expect_tx(&full[slot], panel_bytes);
+        bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats,
+                 Wc + static_cast<size_t>(j) * R * kPanelCols, panel_bytes, &full[slot], pol);
+        if (++j == a.P) j = 0;
+        if (++slot == a.ns) {
+          slot = 0;
+          ++lap;
+        }
+      }
+      if (!ok) {
+        if (!*s_abort) report_error(a.err, kErrTimeout, c, a.tag_base, kSiteEmpty);
+        *s_abort = 1;
+      }
+      // Never leave with copies in flight: wait for the last ns issued.
+      const long long first = it > a.ns ? it - a.ns : 0;
+      for (long long d = first; d < it; ++d) {
+        const int s = static_cast<int>(d % a.ns);
+        const uint32_t par = static_cast<uint32_t>((d / a.ns) & 1);
+        if (!mbar_wait_bounded(&full[s], par, a.timeout_ns, nullptr)) {
+          report_error(a.err, kErrTimeout, c, a.tag_base, kSiteDrain);
+          break;
+        }
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  const int ctid = tid;
+  const int node = r0 + ctid;
+  const bool owner = ctid < R;
+  const bool publish = (G > 1) && (c != a.inject_cta);
+  double mnx = 0, mny = 0, mnz = 0, msx = 0, msy = 0, msz = 0, ax = 0, ay = 0, az = 0, hin = 0;
+  if (owner) {
+    mnx = a.state[node];
+    mny = a.state[a.N + node];
+    mnz = a.state[2 * a.N + node];
+    msx = mnx; msy = mny; msz = mnz;
+  }
+  unsigned tag = a.tag_base;
+  if (owner) {
+    if (G == 1) xs[node] = static_cast<float>(msx);
+    else if (publish)
+      st_relaxed_u64(a.xbuf + static_cast<size_t>(tag & 1u) * a.N + node,
+                     pack_x(static_cast<float>(msx), tag));
+  }
+
+  int cslot = 0;
+  uint32_t cphase = 0;
+  bool aborted = false;
+  for (int t = 0; t < a.T && !aborted; ++t) {
+    if (owner) {
+      double s = 0.0;
+      for (int jj = 0; jj < a.n_in; ++jj)
+        s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
+             static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
+      hin = a.ain_g * s;
+    }
+    for (int sub = 0; sub < a.S && !aborted; ++sub) {
+      for (int st = 0; st < 4; ++st) {
+        // 1. the stage's m^x of every oscillator
+        bool fail = false;
+        if (G > 1 && !gather_x(a, xs, tag, ctid)) {
+          fail = true;
+          *s_abort = 1;
+        }
+        if (consumer_sync_or(fail)) { aborted = true; break; }
+
+        // 2. h = W x over this CTA's rows, panel by panel
+        float acc[RPW];
+#pragma unroll
+        for (int qq = 0; qq < RPW; ++qq) acc[qq] = 0.f;
+        for (int j = 0; j < a.P; ++j) {
+          const int slot = a.resident ? j : cslot;
+          const uint32_t par = a.resident ? 0u : cphase;
+          // every lane waits; the vote keeps the warp's decision uniform
+          const bool landed = mbar_wait_bounded(&full[slot], par, a.timeout_ns, s_abort);
+          if (!__all_sync(0xffffffffu, landed)) {
+            if (lane == 0) {
+              if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
+              *s_abort = 1;
+            }
+            fail = true;
+            break;
+          }
+          const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
+          const float4 xv = reinterpret_cast<const float4*>(xs)[j * (kPanelCols / 4) + lane];
+#pragma unroll
+          for (int qq = 0; qq < RPW; ++qq) {
+            const int r = warp + qq * kConsWarps;
+            if (r < R) {
+              const float4 w = p4[r * (kPanelCols / 4) + lane];
+              float v = acc[qq];
+              v = fmaf(w.x, xv.x, v);
+              v = fmaf(w.y, xv.y, v);
+              v = fmaf(w.z, xv.z, v);
+              v = fmaf(w.w, xv.w, v);
+              acc[qq] = v;
+            }
+          }
+          __syncwarp();
+          if (!a.resident) {
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (++cslot == a.ns) {
+              cslot = 0;
+              cphase ^= 1u;
+            }
+          }
+        }
+#pragma unroll
+        for (int qq = 0; qq < RPW; ++qq) {
+          const int r = warp + qq * kConsWarps;
+          if (r < R) {
+            float v = acc[qq];
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (lane == 0) hs[r] = v;
+          }
+        }
+        if (consumer_sync_or(fail)) { aborted = true; break; }
+
+        // 3. torque, RK4 stage combination, publish the next stage's m^x
+        if (owner) {
+          double dx, dy, dz;
+          llg_increment(a, msx, msy, msz, a.acp * static_cast<double>(hs[ctid]) + hin, dx, dy, dz);
+          if (st == 0) {
+            ax = dx; ay = dy; az = dz;
+            msx = mnx + 0.5 * dx; msy = mny + 0.5 * dy; msz = mnz + 0.5 * dz;
+          } else if (st == 1) {
+            ax += 2.0 * dx; ay += 2.0 * dy; az += 2.0 * dz;
+            msx = mnx + 0.5 * dx; msy = mny + 0.5 * dy; msz = mnz + 0.5 * dz;
+          } else if (st == 2) {
+            ax += 2.0 * dx; ay += 2.0 * dy; az += 2.0 * dz;
+            msx = mnx + dx; msy = mny + dy; msz = mnz + dz;
+          } else {
+            ax += dx; ay += dy; az += dz;
+            mnx += ax * (1.0 / 6.0); mny += ay * (1.0 / 6.0); mnz += az * (1.0 / 6.0);
+            msx = mnx; msy = mny; msz = mnz;
+          }
+          const unsigned nt = tag + 1u;
+          if (G == 1) xs[node] = static_cast<float>(msx);
+          else if (publish)
+            st_relaxed_u64(a.xbuf + static_cast<size_t>(nt & 1u) * a.N + node,
+                           pack_x(static_cast<float>(msx), nt));
+        }
+        ++tag;
+      }
+    }
+    if (!aborted && owner && a.states_out) {
+      const double v = a.comp == 0 ? mnx : (a.comp == 1 ? mny : mnz);
+      a.states_out[static_cast<size_t>(t) * a.N + node] = static_cast<float>(v);
+    }
+  }
+  if (!aborted && owner) {
+    a.state[node] = mnx;
+    a.state[a.N + node] = mny;
+    a.state[2 * a.N + node] = mnz;
+  }
+}
+
+// Scatter a row-major N x N matrix into the tiled layout: CTA c's rows
+// [r0, r0 + R) become P panels of R x kPanelCols floats, panel j holding
+// columns [j*kPanelCols, (j+1)*kPanelCols) (zero beyond N).  The destination
+// must be zeroed beforehand.
+__global__ void tile_w_kernel(const float* __restrict__ W, float* __restrict__ Wt, int N, int G,
+                              int P) {
+  const int q = N / G, rem = N % G;
+  const long long total = static_cast<long long>(N) * N;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(idx / N), i = static_cast<int>(idx % N);
+    int r0, R;
+    if (k < rem * (q + 1)) {
+      const int cc = k / (q + 1);
+      r0 = cc * (q + 1);
+      R = q + 1;
+    } else {
+      const int cc = rem + (k - rem * (q + 1)) / q;
+      r0 = cc * q + rem;
+      R = q;
+    }
+    const int r = k - r0, j = i / kPanelCols, col = i % kPanelCols;
+    Wt[static_cast<size_t>(r0) * P * kPanelCols + static_cast<size_t>(j) * R * kPanelCols +
+       static_cast<size_t>(r) * kPanelCols + col] = W[idx];
+  }
+}
+
+// flag = 1 if any of the n floats is NaN or Inf.
+__global__ void nonfinite_kernel(const float* __restrict__ p, long long n, int* flag) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (!isfinite(p[i])) *flag = 1;
+  }
+}
+
+}  // namespace sto

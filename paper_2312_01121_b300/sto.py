@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libsto (include/sto.h); argument marshalling only.
+
+Every computation runs inside libsto's CUDA kernels.  There is no fallback:
+if ``libsto.so`` is missing or no CUDA device is usable, the calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+they are passed to the library as raw pointers.  The Python functions carry
+the C names (``sto_create``, ``sto_run`` ...); ``Reservoir`` wraps a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsto.so")
+
+STO_OK, STO_EINVAL, STO_ENOMEM, STO_ECUDA, STO_ETIMEOUT, STO_ENONFINITE, STO_ENOTSUP = (
+    0, -1, -2, -3, -4, -5, -6)
+
+
+class StoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsto error {code}: {msg}")
+        self.code = code
+
+
+class sto_params(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("Ms", ctypes.c_double),
+        ("Hk", ctypes.c_double), ("Happl", ctypes.c_double), ("eta", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("current", ctypes.c_double), ("volume", ctypes.c_double),
+        ("e_charge", ctypes.c_double), ("hbar", ctypes.c_double), ("p", ctypes.c_double * 3),
+        ("A_cp", ctypes.c_double), ("A_in", ctypes.c_double), ("input_gain", ctypes.c_double),
+        ("dt", ctypes.c_double), ("substeps", ctypes.c_int32), ("n_in", ctypes.c_int32),
+        ("sample_component", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class sto_config(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class sto_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("grid", ctypes.c_int32), ("rows_max", ctypes.c_int32),
+                ("panel_cols", ctypes.c_int32), ("panels", ctypes.c_int32),
+                ("ring_slots", ctypes.c_int32), ("resident", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("sm_count", ctypes.c_int32),
+                ("w_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+# name -> (restype, argtypes); the exported symbols of include/sto.h
+_VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+SIGNATURES = {
+    "sto_default_params": (None, [ctypes.POINTER(sto_params)]),
+    "sto_create": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
+                                  ctypes.POINTER(_VP)]),
+    "sto_create_ex": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
+                                     ctypes.POINTER(sto_config), ctypes.POINTER(_VP)]),
+    "sto_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(sto_params)]),
+    "sto_set_state": (ctypes.c_int, [_VP, _VP]),
+    "sto_get_state": (ctypes.c_int, [_VP, _VP]),
+    "sto_set_state_f64": (ctypes.c_int, [_VP, _VP]),
+    "sto_get_state_f64": (ctypes.c_int, [_VP, _VP]),
+    "sto_run": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "sto_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(sto_info)]),
+    "sto_destroy": (None, [_VP]),
+    "sto_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sto_abi_version": (ctypes.c_int, []),
+    "sto_debug_inject_stall": (ctypes.c_int, [_VP, _I32]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libsto.so (built in-tree by paper_2312_01121_b300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libsto.so not built ({p}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != STO_OK:
+        raise StoError(rc, load_library().sto_strerror(rc).decode())
+
+
+@dataclasses.dataclass
+class Params:
+    """Python mirror of sto_params; defaults = Table "Summary of parameters"."""
+    gamma: float = 1.764e7
+    alpha: float = 0.005
+    Ms: float = 1448.3
+    Hk: float = 18616.0
+    Happl: float = 200.0
+    eta: float = 0.537
+    lambda_: float = 0.288
+    current: float = 2.5e-3
+    volume: float = math.pi * 60.0 ** 2 * 2.0 * 1e-21
+    e_charge: float = 1.60217733e-19
+    hbar: float = 1.05457266e-34
+    p: tuple = (1.0, 0.0, 6.123234e-17)
+    A_cp: float = 1.0
+    A_in: float = 1.0
+    input_gain: float = 1.0
+    dt: float = 1e-11
+    substeps: int = 100
+    n_in: int = 1
+    sample_component: int = 0
+
+    def replace(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
+
+    def to_c(self) -> sto_params:
+        c = sto_params()
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            if f.name == "p":
+                c.p = (ctypes.c_double * 3)(*[float(x) for x in v])
+            else:
+                setattr(c, f.name, v)
+        c.reserved = 0
+        return c
+
+
+def sto_default_params() -> Params:
+    c = sto_params()
+    load_library().sto_default_params(ctypes.byref(c))
+    kw = {f[0]: getattr(c, f[0]) for f in sto_params._fields_ if f[0] not in ("p", "reserved")}
+    return Params(p=tuple(c.p), **kw)
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive) for a numpy array or torch tensor of `dtype`."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout_ms=0):
+    """Returns an opaque handle (int).  W, w_in, m0: numpy or torch float32."""
+    lib = load_library()
+    pW, kW = _ptr(W, np.float32)
+    pwin, kwin = _ptr(w_in, np.float32)
+    pm0, km0 = _ptr(m0, np.float32)
+    h = _VP()
+    cp = params.to_c()
+    if grid or timeout_ms:
+        cfg = sto_config(grid=grid, timeout_ms=timeout_ms)
+        rc = lib.sto_create_ex(N, ctypes.byref(cp), pW, pwin, pm0, _stream_ptr(stream),
+                               ctypes.byref(cfg), ctypes.byref(h))
+    else:
+        rc = lib.sto_create(N, ctypes.byref(cp), pW, pwin, pm0, _stream_ptr(stream),
+                            ctypes.byref(h))
+    _check(rc)
+    del kW, kwin, km0
+    return h.value
+
+
+def sto_run(h, u, T, states_out=None):
+    pu, ku = _ptr(u, np.float32)
+    if states_out is not None and not hasattr(states_out, "data_ptr"):
+        if not (isinstance(states_out, np.ndarray) and states_out.dtype == np.float32
+                and states_out.flags.c_contiguous):
+            raise TypeError("states_out must be a contiguous float32 array")
+    ps, ks = _ptr(states_out, np.float32)
+    _check(load_library().sto_run(h, pu, T, ps))
+
+
+def sto_set_params(h, params: Params):
+    cp = params.to_c()
+    _check(load_library().sto_set_params(h, ctypes.byref(cp)))
+
+
+def sto_set_state(h, m):
+    p, k = _ptr(m, np.float32)
+    _check(load_library().sto_set_state(h, p))
+
+
+def sto_get_state(h, out):
+    p, k = _ptr(out, np.float32)
+    _check(load_library().sto_get_state(h, p))
+
+
+def sto_set_state_f64(h, m):
+    p, k = _ptr(m, np.float64)
+    _check(load_library().sto_set_state_f64(h, p))
+
+
+def sto_get_state_f64(h, out):
+    p, k = _ptr(out, np.float64)
+    _check(load_library().sto_get_state_f64(h, p))
+
+
+def sto_get_info(h) -> dict:
+    info = sto_info()
+    _check(load_library().sto_get_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def sto_destroy(h):
+    if h:
+        load_library().sto_destroy(h)
+
+
+def sto_debug_inject_stall(h, cta: int):
+    _check(load_library().sto_debug_inject_stall(h, cta))
+
+
+def sto_strerror(code: int) -> str:
+    return load_library().sto_strerror(code).decode()
+
+
+class Reservoir:
+    """One reservoir of N coupled STOs on the current CUDA device."""
+
+    def __init__(self, W, w_in, params: Params | None = None, m0=None, stream=None,
+                 grid: int = 0, timeout_ms: int = 0):
+        self.params = params or Params()
+        self.N = int(W.shape[0])
+        self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms)
+
+    def run(self, u, states_out=None, T=None):
+        """Advance over T = len(u) input samples; fills states_out (T x N) if given."""
+        if T is None:
+            T = int(u.shape[0])
+        sto_run(self.handle, u, T, states_out)
+        return states_out
+
+    def set_params(self, params: Params):
+        sto_set_params(self.handle, params)
+        self.params = params
+
+    def state(self) -> np.ndarray:
+        out = np.empty((3, self.N), dtype=np.float64)
+        sto_get_state_f64(self.handle, out)
+        return out
+
+    def set_state(self, m):
+        m = np.asarray(m)
+        if m.dtype == np.float64:
+            sto_set_state_f64(self.handle, np.ascontiguousarray(m))
+        else:
+            sto_set_state(self.handle, m)
+
+    def info(self) -> dict:
+        return sto_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            sto_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,101 @@
+"""Host-side checks of libsto that need no GPU: it loads, exports every
+symbol include/sto.h declares, and validates arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2312_01121_b300 import build, sto
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return sto.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "sto.h")).read()
+    return sorted(set(re.findall(r"^STO_API\s+[\w\s\*]*?\b(sto_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ["sto_create", "sto_run", "sto_set_state", "sto_get_state", "sto_destroy",
+                     "sto_strerror", "sto_default_params", "sto_create_ex"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(sto.SIGNATURES), "binding and header disagree"
+
+
+def test_exports_are_only_the_abi():
+    out = os.popen(f"nm -D --defined-only {sto.LIB_PATH}").read()
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {n for n in exported if n.startswith("sto_")} == set(declared_symbols())
+
+
+def test_abi_version_and_strerror(lib):
+    assert lib.sto_abi_version() == 1
+    for code in [0, -1, -2, -3, -4, -5, -6]:
+        assert sto.sto_strerror(code)
+    assert "invalid" in sto.sto_strerror(-1)
+
+
+def test_default_params_are_the_paper_table(lib):
+    p = sto.sto_default_params()
+    assert p == sto.Params()
+    assert (p.gamma, p.alpha, p.Ms, p.Hk, p.Happl) == (1.764e7, 0.005, 1448.3, 18616.0, 200.0)
+    assert (p.eta, p.lambda_, p.current, p.A_cp, p.A_in, p.dt) == (0.537, 0.288, 2.5e-3, 1.0, 1.0, 1e-11)
+    assert p.p == (1.0, 0.0, 6.123234e-17)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors vs the C compiler's sizeof / offsetof of include/sto.h."""
+    fields = {"sto_params": [f[0] for f in sto.sto_params._fields_],
+              "sto_config": [f[0] for f in sto.sto_config._fields_],
+              "sto_info": [f[0] for f in sto.sto_info._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sto.h"', "int main(void){"]
+    for st, names in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for n in names:
+            cn = "lambda" if n == "lambda_" else n
+            lines.append(f'printf("{st}.{n} %zu\\n", offsetof({st}, {cn}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    assert os.system(f"gcc -I {ROOT}/include -o {exe} {src}") == 0
+    got = dict(l.split() for l in os.popen(str(exe)).read().splitlines())
+    for st, names in fields.items():
+        cls = getattr(sto, st)
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for n in names:
+            assert int(got[f"{st}.{n}"]) == getattr(cls, n).offset, f"{st}.{n}"
+
+
+def test_invalid_arguments_rejected_before_cuda(lib):
+    cp = sto.Params().to_c()
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_float * 4)()
+    assert lib.sto_create(0, ctypes.byref(cp), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_create(2, ctypes.byref(cp), None, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_create(2, None, buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_create(2, ctypes.byref(cp), buf, buf, None, None, None) == sto.STO_EINVAL
+    bad = sto.Params(substeps=0).to_c()
+    assert lib.sto_create(2, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    bad = sto.Params(dt=float("nan")).to_c()
+    assert lib.sto_create(2, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    bad = sto.Params(sample_component=3).to_c()
+    assert lib.sto_create(2, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_run(None, buf, 1, None) == sto.STO_EINVAL
+    assert lib.sto_get_info(None, None) == sto.STO_EINVAL
+    lib.sto_destroy(None)

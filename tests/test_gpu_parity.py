@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written per test):
+  * one RK4 step from the same float32-representable state: the increment
+    m_{n+1} - m_n agrees to 1e-5 relative to its largest component;
+  * the sampled states over the first 200 input samples (and the final
+    state) agree to 1e-4 absolute (|m| = 1, so this is also relative);
+  * long horizons where trajectories may legitimately diverge: readout NMSE
+    within 1e-3 absolute.
+"""
+import numpy as np
+import pytest
+
+import helpers
+from helpers import make_system, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2312_01121_b300 import build, sto
+    build.build()
+    sto.load_library()
+
+
+def sto_mod():
+    from paper_2312_01121_b300 import sto
+    return sto
+
+
+def Params(**kw):
+    return sto_mod().Params(**kw)
+
+
+# ------------------------------------------------------------------ one step
+
+@pytest.mark.parametrize("N,kind,A_cp", [(1, "paper", 1.0), (8, "paper", 1.0), (8, "paper", 200.0),
+                                         (100, "gauss", 1.0), (100, "gauss", 300.0),
+                                         (1000, "gauss", 300.0), (2500, "gauss", 300.0)])
+def test_one_rk4_step_increment(N, kind, A_cp):
+    W, w_in, m0, u = make_system(N, kind, seed=N)
+    P = Params(substeps=1, A_cp=A_cp)
+    m_gpu, _ = run_gpu(P, W, w_in, m0, u[:1])
+    m_orc, _ = run_oracle(P, W, w_in, m0, u[:1])
+    d_gpu = m_gpu - m0.astype(np.float64)
+    d_orc = m_orc - m0.astype(np.float64)
+    rel = np.max(np.abs(d_gpu - d_orc)) / np.max(np.abs(d_orc))
+    assert rel <= 1e-5, rel
+
+
+# ------------------------------------------------------------ 200 input samples
+
+@pytest.mark.parametrize("N,kind,T,S", [(8, "paper", 200, 100), (100, "gauss", 200, 100),
+                                        (1000, "gauss", 30, 100)])
+def test_first_200_input_samples(N, kind, T, S):
+    W, w_in, m0, u = make_system(N, kind, seed=0, T=T)
+    P = Params(substeps=S)
+    m_gpu, st_gpu = run_gpu(P, W, w_in, m0, u)
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st_gpu - st_orc)) <= 1e-4
+    assert np.max(np.abs(m_gpu - m_orc)) <= 1e-4
+    # |m| = 1 is kept to RK4 accuracy, no renormalisation (Sec. 3.2)
+    assert np.max(np.abs(np.linalg.norm(m_gpu, axis=0) - 1.0)) < 1e-4
+
+
+# ------------------------------------------------------ plans, ragged sizes
+
+@pytest.mark.parametrize("N,grid", [(1, 0), (2, 0), (3, 1), (13, 0), (13, 5), (127, 0), (128, 3),
+                                    (129, 0), (300, 148), (257, 0), (257, 2), (1001, 0),
+                                    (1001, 7), (2500, 0), (4099, 0)])
+def test_ragged_sizes_and_plans(N, grid):
+    if grid > torch.cuda.get_device_properties(0).multi_processor_count:
+        pytest.skip("fewer SMs than the requested grid")
+    W, w_in, m0, u = make_system(N, "gauss", seed=N + grid, T=3)
+    P = Params(substeps=3, A_cp=100.0)
+    m_gpu, st_gpu = run_gpu(P, W, w_in, m0, u, grid=grid)
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st_gpu - st_orc)) <= 1e-5
+    assert np.max(np.abs(m_gpu - m_orc)) <= 1e-5
+
+
+def test_streamed_ring_plan_small_grid():
+    """A plan whose rows do not fit on chip: W streams through the ring."""
+    N = 3000
+    W, w_in, m0, u = make_system(N, "gauss", seed=3, T=2)
+    P = Params(substeps=2, A_cp=50.0)
+    sto = sto_mod()
+    r = sto.Reservoir(W, w_in, P, m0=m0, grid=24)
+    info = r.info()
+    r.close()
+    assert info["resident"] == 0 and info["ring_slots"] >= 2
+    m_gpu, st_gpu = run_gpu(P, W, w_in, m0, u, grid=24)
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st_gpu - st_orc)) <= 1e-5
+
+
+def test_full_size_n10000_launch_config():
+    """N = 10^4 (400 MB FP32 W) in the automatic plan the benchmark times:
+    one input sample of 2 RK4 steps, every output compared."""
+    N = 10000
+    W, w_in, m0, u = make_system(N, "gauss", seed=0, T=1)
+    P = Params(substeps=2)
+    m_gpu, st_gpu = run_gpu(P, W, w_in, m0, u)
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st_gpu - st_orc)) <= 1e-5
+    assert np.max(np.abs(m_gpu - m_orc)) <= 1e-5
+
+
+# ------------------------------------------------------ options and edge cases
+
+def test_sample_component_inputs_and_gain():
+    N = 50
+    W, w_in, m0, u = make_system(N, "paper", seed=2, T=4, n_in=3)
+    for comp in (0, 1, 2):
+        P = Params(substeps=5, n_in=3, input_gain=1.7, A_in=40.0, sample_component=comp)
+        m_gpu, st_gpu = run_gpu(P, W, w_in, m0, u)
+        m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+        assert np.max(np.abs(st_gpu - st_orc)) <= 1e-5
+
+
+def test_default_initial_condition_eq_initial():
+    """m0 = NULL selects Eq. (initial) for every oscillator."""
+    import oracle
+    N = 16
+    W, w_in, _, u = make_system(N, "paper", seed=1, T=2)
+    P = Params(substeps=4)
+    sto = sto_mod()
+    with sto.Reservoir(W, w_in, P) as r:
+        m_init = r.state()
+        st = np.zeros((2, N), np.float32)
+        r.run(u, st)
+    assert np.array_equal(m_init, oracle.initial_state(N))
+    _, st_orc = run_oracle(P, W, w_in, None, u, m0_f64=oracle.initial_state(N))
+    assert np.max(np.abs(st - st_orc)) <= 1e-5
+
+
+def test_host_and_device_pointers_agree_bitwise():
+    W, w_in, m0, u = make_system(300, "gauss", seed=5, T=3)
+    P = Params(substeps=4)
+    a = run_gpu(P, W, w_in, m0, u, device=True)
+    b = run_gpu(P, W, w_in, m0, u, device=False)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_deterministic_and_resumable():
+    """Same inputs give the same bits; T samples in one call equal 2 + (T-2)."""
+    N = 700
+    W, w_in, m0, u = make_system(N, "gauss", seed=6, T=6)
+    P = Params(substeps=5)
+    sto = sto_mod()
+    full = run_gpu(P, W, w_in, m0, u)
+    again = run_gpu(P, W, w_in, m0, u)
+    assert np.array_equal(full[1], again[1]) and np.array_equal(full[0], again[0])
+    with sto.Reservoir(W, w_in, P, m0=m0) as r:
+        s1 = np.zeros((2, N), np.float32)
+        s2 = np.zeros((4, N), np.float32)
+        r.run(u[:2], s1)
+        r.run(u[2:], s2)
+        m = r.state()
+    assert np.array_equal(np.vstack([s1, s2]), full[1]) and np.array_equal(m, full[0])
+
+
+def test_state_roundtrip_and_zero_samples():
+    N = 33
+    W, w_in, m0, u = make_system(N, "gauss", seed=7, T=2)
+    sto = sto_mod()
+    with sto.Reservoir(W, w_in, Params(), m0=m0) as r:
+        assert np.array_equal(r.state(), m0.astype(np.float64))
+        r.run(u[:0], None, T=0)                  # T = 0 is a no-op
+        assert np.array_equal(r.state(), m0.astype(np.float64))
+        r.run(u, None)                           # states_out may be NULL
+        m = r.state()
+        r.set_state(m)                            # FP64 round trip
+        assert np.array_equal(r.state(), m)
+        f = np.zeros((3, N), np.float32)
+        sto.sto_get_state(r.handle, f)
+        assert np.array_equal(f, m.astype(np.float32))
+
+
+def test_set_params_changes_the_physics_not_the_plan():
+    N = 200
+    W, w_in, m0, u = make_system(N, "gauss", seed=8, T=2)
+    P1 = Params(substeps=3, current=1.5e-3, A_cp=20.0)
+    sto = sto_mod()
+    with sto.Reservoir(W, w_in, Params(), m0=m0) as r:
+        r.set_params(P1)
+        st = np.zeros((2, N), np.float32)
+        r.run(u, st)
+    _, st_orc = run_oracle(P1, W, w_in, m0, u)
+    assert np.max(np.abs(st - st_orc)) <= 1e-5
+
+
+def test_plan_limits_are_reported():
+    """Rows of one CTA that leave no room for two ring slots: STO_ENOTSUP."""
+    sto = sto_mod()
+    W, w_in, m0, _ = make_system(3000, "gauss", seed=4, T=1)
+    with pytest.raises(sto.StoError) as e:
+        sto.Reservoir(W, w_in, Params(), m0=m0, grid=12)
+    assert e.value.code == sto.STO_ENOTSUP
+
+
+def test_invalid_and_nonfinite_inputs():
+    sto = sto_mod()
+    W, w_in, m0, u = make_system(10, "gauss", seed=9, T=2)
+    Wbad = W.copy()
+    Wbad[3, 4] = np.nan
+    with pytest.raises(sto.StoError) as e:
+        sto.Reservoir(Wbad, w_in, Params())
+    assert e.value.code == sto.STO_ENONFINITE
+    m_bad = m0.copy()
+    m_bad[0, 0] = np.inf
+    with pytest.raises(sto.StoError) as e:
+        sto.Reservoir(W, w_in, Params(), m0=m_bad)
+    assert e.value.code == sto.STO_ENONFINITE
+    with pytest.raises(sto.StoError) as e:
+        sto.Reservoir(W, w_in, Params(), grid=11)       # more CTAs than oscillators
+    assert e.value.code == sto.STO_EINVAL
+    with sto.Reservoir(W, w_in, Params(), m0=m0) as r:
+        with pytest.raises(sto.StoError) as e:
+            sto.sto_set_params(r.handle, Params(n_in=2))
+        assert e.value.code == sto.STO_EINVAL
+        with pytest.raises(sto.StoError) as e:
+            sto.sto_run(r.handle, u, -1, None)
+        assert e.value.code == sto.STO_EINVAL
+
+
+def test_device_timeout_is_reported_and_recoverable():
+    """A CTA that never publishes (host-set flag) makes every other CTA's
+    bounded wait expire: sto_run returns STO_ETIMEOUT instead of hanging, and
+    the same handle then runs normally."""
+    sto = sto_mod()
+    N = 64
+    W, w_in, m0, u = make_system(N, "gauss", seed=10, T=2)
+    P = Params(substeps=2)
+    with sto.Reservoir(W, w_in, P, m0=m0, grid=4, timeout_ms=100) as r:
+        sto.sto_debug_inject_stall(r.handle, 1)
+        with pytest.raises(sto.StoError) as e:
+            r.run(u, np.zeros((2, N), np.float32))
+        assert e.value.code == sto.STO_ETIMEOUT
+        r.set_state(m0)
+        st = np.zeros((2, N), np.float32)
+        r.run(u, st)
+    _, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st - st_orc)) <= 1e-5
+
+
+# ------------------------------------------------------ readout over long horizons
+
+def test_readout_nmse_matches_oracle():
+    """Delay-5 recall with the ridge readout (same FP64 fit on both state
+    sets): NMSE within 1e-3 absolute."""
+    from oracle import readout
+    N, T = 100, 600
+    W, w_in, m0, u = make_system(N, "gauss", seed=11, T=T)
+    P = Params(substeps=20, A_in=50.0)
+    _, st_gpu = run_gpu(P, W, w_in, m0, u)
+    _, st_orc = run_oracle(P, W, w_in, m0, u)
+    _, n_gpu = readout.evaluate(st_gpu, u, washout=100)
+    _, n_orc = readout.evaluate(st_orc, u, washout=100)
+    assert abs(n_gpu - n_orc) <= 1e-3
+    assert n_orc < 1.0
