@@ -71,6 +71,7 @@ extern "C" {
 #define STO_ETIMEOUT (-4)    /* a device-side wait exceeded its time limit */
 #define STO_ENONFINITE (-5)  /* NaN or Inf found in an input */
 #define STO_ENOTSUP (-6)     /* size or option outside what this build supports */
+#define STO_ETOOBIG (-7)     /* N above the static scratch of sto_run_noalloc */
 
 /* Model parameters.  Defaults (sto_default_params) are Table "Summary of
  * parameters" of Sec. 3.1 and the step of Sec. 3.2; substeps, n_in,
@@ -196,6 +197,41 @@ STO_API int sto_abi_version(void);
  * STO_ETIMEOUT with the handle still usable after sto_set_state.  cta < 0
  * clears it.  Only meaningful when the plan has more than one CTA. */
 STO_API int sto_debug_inject_stall(sto_handle* h, int32_t cta);
+
+/* Allocation-free variant of sto_run, for callers that must not allocate
+ * device memory: code running under a framework or pool allocator that owns
+ * all of the device's memory, real-time loops in which cudaMalloc's implicit
+ * device synchronisation is not acceptable, or plug-ins that may only use
+ * buffers handed to them.  The paper has no counterpart; it is a deployment
+ * convenience.
+ *
+ * Same stepping as sto_run, but no handle: the caller owns every array, all
+ * in device memory of the current device, and the library allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  The inter-CTA
+ * exchange buffer and the error word live in a fixed 256 KB + 256 B
+ * statically allocated device array inside libsto, present on every device
+ * that loads the library until the process exits.
+ *   N           1 .. 16384 and a multiple of 4 (larger N: STO_ETOOBIG).
+ *   params      as for sto_create.
+ *   W           N x N row-major float32, 16-byte aligned, read in place.
+ *   w_in        N x n_in float32.
+ *   state       3 x N float64 (m^x block, m^y block, m^z block), advanced
+ *               in place.
+ *   u, T, states_out   as for sto_run (states_out may be NULL).
+ *   stream      cudaStream_t to order the work on (NULL = legacy default).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array, which keeps the previous call's
+ * contents; the call clears what must start fresh.  Calls that overlap on
+ * the GPU (two streams, two threads) race on the array and must be
+ * serialised by the caller.  The call synchronises `stream` to read the
+ * device error word.
+ * Errors: STO_EINVAL (pointer not device memory, N not a multiple of 4,
+ *         misaligned W), STO_ETOOBIG, STO_ENONFINITE (W or w_in), STO_ETIMEOUT,
+ *         STO_ECUDA, STO_ENOTSUP. */
+STO_API int sto_run_noalloc(int64_t N, const sto_params* params, const float* W,
+                            const float* w_in, double* state, const float* u,
+                            int64_t T, float* states_out, void* stream);
 
 #ifdef __cplusplus
 }

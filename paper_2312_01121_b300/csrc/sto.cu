@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -172,9 +173,9 @@ void free_handle(sto_handle* h) {
   delete h;
 }
 
-template <int RPW>
+template <int RPW, bool kRowMajorW = false>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW>,
+  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(pl.smem));
   if (e != cudaSuccess) return e;
@@ -188,7 +189,15 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW>, a);
+}
+
+cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  if (pl.rpw <= 1) return launch_rpw<1, true>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2, true>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4, true>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8, true>(pl, a, s);
+  return launch_rpw<16, true>(pl, a, s);
 }
 
 cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -252,6 +261,52 @@ int grow(float** buf, size_t* cap, size_t n) {
   return STO_OK;
 }
 
+// Constants of Eq. (gov) in the form the stepper uses.
+void set_constants(const sto_params& P, sto::KArgs* a) {
+  const double gp = P.gamma / (1.0 + P.alpha * P.alpha);
+  a->gdt = -gp * P.dt;
+  a->alpha = P.alpha;
+  a->happl = P.Happl;
+  a->hkp = P.Hk - 4.0 * M_PI * P.Ms;
+  a->hs0 = P.hbar * P.eta * P.current * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume);
+  a->lambda = P.lambda;
+  a->px = P.p[0];
+  a->py = P.p[1];
+  a->pz = P.p[2];
+  a->acp = P.A_cp;
+  a->ain_g = P.A_in * P.input_gain;
+}
+
+// ------------------------------------------------- allocation-free entry point
+//
+// Scratch of sto_run_noalloc: a file-scope device array, present on every
+// device that loads the library until the process exits.  Layout: bytes
+// [0, 16) error word, [16, 20) non-finite flag, [256, 256 + 16 N) the two
+// parity buffers of tagged m^x words.  In host code the name is only a
+// stand-in; the device address comes from cudaGetSymbolAddress.
+constexpr int64_t kNoAllocMaxN = 16384;
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * static_cast<size_t>(kNoAllocMaxN) * 8;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_dev[kMaxDevices] = {};
+
+// Device address of the scratch on device `dev` (current), looked up once.
+int noalloc_scratch(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= kMaxDevices) return STO_ENOTSUP;
+  if (!g_noalloc_dev[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_noalloc_dev[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_dev[dev];
+  return STO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -272,6 +327,7 @@ const char* sto_strerror(int code) {
     case STO_ETIMEOUT: base = "device wait timed out"; break;
     case STO_ENONFINITE: base = "non-finite input"; break;
     case STO_ENOTSUP: base = "not supported by this build"; break;
+    case STO_ETOOBIG: base = "size exceeds the static scratch of sto_run_noalloc (N <= 16384)"; break;
     default: break;
   }
   if (code == STO_ECUDA && g_last_cuda != cudaSuccess)
@@ -539,18 +595,7 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
   a.inject_cta = h->inject_cta;
   a.tag_base = static_cast<unsigned>(base);
   a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
-  const double gp = P.gamma / (1.0 + P.alpha * P.alpha);
-  a.gdt = -gp * P.dt;
-  a.alpha = P.alpha;
-  a.happl = P.Happl;
-  a.hkp = P.Hk - 4.0 * M_PI * P.Ms;
-  a.hs0 = P.hbar * P.eta * P.current * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume);
-  a.lambda = P.lambda;
-  a.px = P.p[0];
-  a.py = P.p[1];
-  a.pz = P.p[2];
-  a.acp = P.A_cp;
-  a.ain_g = P.A_in * P.input_gain;
+  set_constants(P, &a);
 
   STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
   STO_CUDA(launch_stepper(h->plan, a, s));
@@ -560,6 +605,78 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
   STO_CUDA(cudaStreamSynchronize(s));
   h->inject_cta = -1;
   if (h->h_err[0] != 0) return h->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  return STO_OK;
+}
+
+int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const float* w_in,
+                    double* state, const float* u, int64_t T, float* states_out, void* stream) {
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (N < 1 || T < 0 || !W || !w_in || !state || (T > 0 && !u)) return STO_EINVAL;
+  if (N > kNoAllocMaxN) return STO_ETOOBIG;
+  if (N % 4 != 0 || (reinterpret_cast<uintptr_t>(W) & 15u) != 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  const sto_params& P = *params;
+  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
+  if (!is_device_ptr(W) || !is_device_ptr(w_in) || !is_device_ptr(state) || !is_device_ptr(u) ||
+      (states_out && !is_device_ptr(states_out)))
+    return STO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sm_count = 0, smem_optin = 0;
+  STO_CUDA(cudaGetDevice(&dev));
+  STO_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+  STO_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  Plan plan;
+  rc = make_plan(N, 0, sm_count, static_cast<size_t>(smem_optin), &plan);
+  if (rc) return rc;
+  unsigned char* scratch = nullptr;
+  rc = noalloc_scratch(dev, &scratch);
+  if (rc) return rc;
+  int* d_err = reinterpret_cast<int*>(scratch);
+  int* d_flag = reinterpret_cast<int*>(scratch + 16);
+  auto* d_xbuf = reinterpret_cast<unsigned long long*>(scratch + kNoAllocHeader);
+
+  // The scratch keeps the previous call's contents: clear the error word and
+  // flag, and mark every exchange word with tag 0xffffffff (never used).
+  STO_CUDA(cudaMemsetAsync(scratch, 0, kNoAllocHeader, s));
+  STO_CUDA(cudaMemsetAsync(d_xbuf, 0xff, 2 * static_cast<size_t>(N) * 8, s));
+  const long long nw = N * N, nwin = N * static_cast<long long>(P.n_in);
+  sto::nonfinite_kernel<<<4096, 256, 0, s>>>(W, nw, d_flag);
+  STO_CUDA(cudaGetLastError());
+  sto::nonfinite_kernel<<<static_cast<unsigned>((nwin + 255) / 256 < 4096 ? (nwin + 255) / 256 : 4096),
+                          256, 0, s>>>(w_in, nwin, d_flag);
+  STO_CUDA(cudaGetLastError());
+  int h_flag = 0;
+  STO_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  if (h_flag) return STO_ENONFINITE;
+
+  sto::KArgs a{};
+  a.W = W;
+  a.w_in = w_in;
+  a.u = u;
+  a.state = state;
+  a.states_out = states_out;
+  a.xbuf = d_xbuf;
+  a.err = d_err;
+  a.N = static_cast<int>(N);
+  a.n_in = P.n_in;
+  a.T = static_cast<int>(T);
+  a.S = P.substeps;
+  a.P = plan.P;
+  a.ns = plan.ns;
+  a.resident = plan.resident;
+  a.comp = P.sample_component;
+  a.inject_cta = -1;
+  a.tag_base = 1u;
+  a.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
+  set_constants(P, &a);
+  STO_CUDA(launch_stepper_rowmajor(plan, a, s));
+  int h_err[4] = {0, 0, 0, 0};
+  STO_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  if (h_err[0] != 0) return h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
   return STO_OK;
 }
 

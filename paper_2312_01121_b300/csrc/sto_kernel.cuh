@@ -249,7 +249,11 @@ __device__ __forceinline__ void llg_increment(const KArgs& a, double mx, double 
 
 // ------------------------------------------------------------ the stepper
 
-template <int RPW>
+// kRowMajorW = false: a.W is the tiled copy made by sto_create (one bulk copy
+// per panel).  kRowMajorW = true: a.W is the caller's row-major N x N matrix
+// (N a multiple of 4); each panel arrives as one bulk copy per row, issued by
+// the 32 lanes of the producer warp.  Consumers are identical in both.
+template <int RPW, bool kRowMajorW>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int c = blockIdx.x;
@@ -278,12 +282,69 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
     fence_mbar_init();
   }
   for (int i = tid; i < a.P * kPanelCols; i += kThreads) xs[i] = 0.f;
+  if constexpr (kRowMajorW) {
+    // columns past N of the last panel are never written by a copy: keep
+    // them finite (they meet x = 0)
+    for (size_t i = tid; i < slot_floats * a.ns; i += kThreads) ring[i] = 0.f;
+  }
   __syncthreads();
 
   const float* Wc = a.W + static_cast<size_t>(r0) * a.P * kPanelCols;
   const uint32_t panel_bytes = static_cast<uint32_t>(R) * kPanelCols * 4u;
 
   // ------------------------------------------------------------ producer
+  if constexpr (kRowMajorW) {
+    if (warp == kConsWarps) {
+      const uint64_t pol = a.resident ? policy_evict_last() : policy_evict_first();
+      const long long total =
+          a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
+      const float* Wrows = a.W + static_cast<size_t>(r0) * a.N;
+      long long it = 0;
+      int slot = 0, j = 0;
+      uint32_t lap = 0;
+      bool ok = true;
+      for (; it < total; ++it) {
+        if (!a.resident && lap > 0) {
+          bool freed = true;
+          if (lane == 0)
+            freed = mbar_wait_bounded(&empty[slot], (lap - 1u) & 1u, a.timeout_ns, s_abort);
+          if (!__shfl_sync(0xffffffffu, freed, 0)) {
+            ok = false;
+            break;
+          }
+        }
+        const int cols = min(kPanelCols, a.N - j * kPanelCols);
+        const uint32_t row_bytes = static_cast<uint32_t>(cols) * 4u;
+        if (lane == 0) mbar_arrive_expect_tx(&full[slot], row_bytes * static_cast<uint32_t>(R));
+        __syncwarp();
+        for (int r = lane; r < R; r += 32)
+          bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats + static_cast<size_t>(r) * kPanelCols,
+                   Wrows + static_cast<size_t>(r) * a.N + static_cast<size_t>(j) * kPanelCols,
+                   row_bytes, &full[slot], pol);
+        if (++j == a.P) j = 0;
+        if (++slot == a.ns) {
+          slot = 0;
+          ++lap;
+        }
+      }
+      if (lane == 0) {
+        if (!ok) {
+          if (!*s_abort) report_error(a.err, kErrTimeout, c, a.tag_base, kSiteEmpty);
+          *s_abort = 1;
+        }
+        const long long first = it > a.ns ? it - a.ns : 0;
+        for (long long d = first; d < it; ++d) {
+          const int s = static_cast<int>(d % a.ns);
+          const uint32_t par = static_cast<uint32_t>((d / a.ns) & 1);
+          if (!mbar_wait_bounded(&full[s], par, a.timeout_ns, nullptr)) {
+            report_error(a.err, kErrTimeout, c, a.tag_base, kSiteDrain);
+            break;
+          }
+        }
+      }
+      return;
+    }
+  }
   if (warp == kConsWarps) {
     if (lane == 0) {
       const uint64_t pol = a.resident ? policy_evict_last() : policy_evict_first();

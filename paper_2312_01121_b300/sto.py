@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libsto.so")
 
 STO_OK, STO_EINVAL, STO_ENOMEM, STO_ECUDA, STO_ETIMEOUT, STO_ENONFINITE, STO_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6)
+STO_ETOOBIG = -7
 
 
 class StoError(RuntimeError):
@@ -76,6 +77,8 @@ SIGNATURES = {
     "sto_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sto_abi_version": (ctypes.c_int, []),
     "sto_debug_inject_stall": (ctypes.c_int, [_VP, _I32]),
+    "sto_run_noalloc": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
+                                       _I64, _VP, _VP]),
 }
 
 _lib = None
@@ -239,6 +242,21 @@ def sto_destroy(h):
 
 def sto_debug_inject_stall(h, cta: int):
     _check(load_library().sto_debug_inject_stall(h, cta))
+
+
+def sto_run_noalloc(N, params: Params, W, w_in, state, u, T, states_out=None, stream=None):
+    """Allocation-free stepping for callers that must not allocate device
+    memory (pool-owned devices, capture-free real-time loops, plug-ins).
+    All arrays are caller-owned CUDA tensors: W (N x N float32), w_in, state
+    (3 x N float64, advanced in place), u, states_out (or None)."""
+    cp = params.to_c()
+    pW, kW = _ptr(W, np.float32)
+    pwin, kwin = _ptr(w_in, np.float32)
+    pst, kst = _ptr(state, np.float64)
+    pu, ku = _ptr(u, np.float32)
+    pso, kso = _ptr(states_out, np.float32)
+    _check(load_library().sto_run_noalloc(N, ctypes.byref(cp), pW, pwin, pst, pu, T, pso,
+                                          _stream_ptr(stream)))
 
 
 def sto_strerror(code: int) -> str:
