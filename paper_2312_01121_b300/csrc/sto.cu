@@ -263,17 +263,19 @@ int grow(float** buf, size_t* cap, size_t n) {
 
 // Constants of Eq. (gov) in the form the stepper uses.
 void set_constants(const sto_params& P, sto::KArgs* a) {
+  using sto::df_split_host;
   const double gp = P.gamma / (1.0 + P.alpha * P.alpha);
-  a->gdt = -gp * P.dt;
-  a->alpha = P.alpha;
-  a->happl = P.Happl;
-  a->hkp = P.Hk - 4.0 * M_PI * P.Ms;
-  a->hs0 = P.hbar * P.eta * P.current * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume);
-  a->lambda = P.lambda;
-  a->px = P.p[0];
-  a->py = P.p[1];
-  a->pz = P.p[2];
-  a->acp = P.A_cp;
+  a->gdt = df_split_host(-gp * P.dt);
+  a->alpha = df_split_host(P.alpha);
+  a->happl = df_split_host(P.Happl);
+  a->hkp = df_split_host(P.Hk - 4.0 * M_PI * P.Ms);
+  a->hs0 = df_split_host(P.hbar * P.eta * P.current * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume));
+  a->lambda = df_split_host(P.lambda);
+  a->px = df_split_host(P.p[0]);
+  a->py = df_split_host(P.p[1]);
+  a->pz = df_split_host(P.p[2]);
+  a->acp = df_split_host(P.A_cp);
+  a->sixth = df_split_host(1.0 / 6.0);
   a->ain_g = P.A_in * P.input_gain;
 }
 

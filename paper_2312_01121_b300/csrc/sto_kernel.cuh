@@ -7,8 +7,9 @@
 //      (tagged 8-byte words published by their owners, see below),
 //   2. computes h_k = sum_i W[k,i] m^x_i for its rows while a producer warp
 //      streams its W rows through a shared-memory ring with TMA bulk copies,
-//   3. evaluates the LLG + spin-transfer torque of its oscillators in FP64,
-//      combines the RK4 stage and publishes the next stage's m^x.
+//   3. evaluates the LLG + spin-transfer torque of its oscillators in
+//      double-float (about 48 significand bits on the FP32 pipes), combines
+//      the RK4 stage and publishes the next stage's m^x.
 // The W stream never waits for step 1: W is constant, so the producer runs
 // ahead across stage boundaries and HBM stays busy while CTAs synchronise.
 //
@@ -28,6 +29,8 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "dfloat.cuh"
 
 namespace sto {
 
@@ -52,9 +55,10 @@ struct KArgs {
   int N, n_in, T, S, P, ns, resident, comp, inject_cta;
   unsigned int tag_base;
   unsigned long long timeout_ns;
-  // FP64 constants of Eq. (gov)
-  double gdt;    // -gamma' * dt
-  double alpha, happl, hkp, hs0, lambda, px, py, pz, acp, ain_g;
+  // constants of Eq. (gov) as double-float pairs
+  df gdt;        // -gamma' * dt
+  df alpha, happl, hkp, hs0, lambda, px, py, pz, acp, sixth;
+  double ain_g;  // g * A_in (input field formed once per sample in FP64)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -224,27 +228,25 @@ __device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag
   return true;
 }
 
-// dt * dm/dt of Eq. (gov) for one oscillator, in FP64.
+// dt * dm/dt of Eq. (gov) for one oscillator, in double-float.
 // hx = coupling + input field along e_x (Eq. coup + Eq. in).
-__device__ __forceinline__ void llg_increment(const KArgs& a, double mx, double my, double mz,
-                                              double hx, double& dx, double& dy, double& dz) {
-  const double s = mx * a.px + my * a.py + mz * a.pz;        // m . p
-  const double hs = a.hs0 / (1.0 + a.lambda * s);            // H_s(m)
-  const double cx = a.py * mz - a.pz * my;                   // p x m
-  const double cy = a.pz * mx - a.px * mz;
-  const double cz = a.px * my - a.py * mx;
-  const double bx = hx + hs * cx;                            // b
-  const double by = hs * cy;
-  const double bz = a.happl + a.hkp * mz + hs * cz;
-  const double tx = my * bz - mz * by;                       // m x b
-  const double ty = mz * bx - mx * bz;
-  const double tz = mx * by - my * bx;
-  const double ux = my * tz - mz * ty;                       // m x (m x b)
-  const double uy = mz * tx - mx * tz;
-  const double uz = mx * ty - my * tx;
-  dx = a.gdt * (tx + a.alpha * ux);                          // -gamma' dt (...)
-  dy = a.gdt * (ty + a.alpha * uy);
-  dz = a.gdt * (tz + a.alpha * uz);
+__device__ __forceinline__ void llg_increment(const KArgs& a, const df m[3], df hx, df d[3]) {
+  const df s = df_add(df_add(df_mul(m[0], a.px), df_mul(m[1], a.py)), df_mul(m[2], a.pz));  // m.p
+  const df hs = df_mul(a.hs0, df_rcp(df_add_f(df_mul(a.lambda, s), 1.0f)));              // H_s(m)
+  const df cx = df_cross1(a.py, m[2], a.pz, m[1]);                                          // p x m
+  const df cy = df_cross1(a.pz, m[0], a.px, m[2]);
+  const df cz = df_cross1(a.px, m[1], a.py, m[0]);
+  const df b[3] = {df_add(hx, df_mul(hs, cx)),                                              // b
+                   df_mul(hs, cy),
+                   df_add(df_add(a.happl, df_mul(a.hkp, m[2])), df_mul(hs, cz))};
+  const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]),                                       // m x b
+                   df_cross1(m[2], b[0], m[0], b[2]),
+                   df_cross1(m[0], b[1], m[1], b[0])};
+  const df u[3] = {df_cross1(m[1], t[2], m[2], t[1]),                                       // m x (m x b)
+                   df_cross1(m[2], t[0], m[0], t[2]),
+                   df_cross1(m[0], t[1], m[1], t[0])};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[i] = df_mul(a.gdt, df_add(t[i], df_mul(a.alpha, u[i])));  // -gamma' dt (...)
 }
 
 // ------------------------------------------------------------ the stepper
@@ -393,19 +395,19 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   const int node = r0 + ctid;
   const bool owner = ctid < R;
   const bool publish = (G > 1) && (c != a.inject_cta);
-  double mnx = 0, mny = 0, mnz = 0, msx = 0, msy = 0, msz = 0, ax = 0, ay = 0, az = 0, hin = 0;
-  if (owner) {
-    mnx = a.state[node];
-    mny = a.state[a.N + node];
-    mnz = a.state[2 * a.N + node];
-    msx = mnx; msy = mny; msz = mnz;
+  // state of the owned oscillator in double-float: m_n, stage state, RK4 sum
+  df mn[3], ms[3], ksum[3], hin = {0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    mn[i] = owner ? df_from_double(a.state[static_cast<size_t>(i) * a.N + node]) : df{0.f, 0.f};
+    ms[i] = mn[i];
+    ksum[i] = df{0.f, 0.f};
   }
   unsigned tag = a.tag_base;
   if (owner) {
-    if (G == 1) xs[node] = static_cast<float>(msx);
+    if (G == 1) xs[node] = ms[0].hi;
     else if (publish)
-      st_relaxed_u64(a.xbuf + static_cast<size_t>(tag & 1u) * a.N + node,
-                     pack_x(static_cast<float>(msx), tag));
+      st_relaxed_u64(a.xbuf + static_cast<size_t>(tag & 1u) * a.N + node, pack_x(ms[0].hi, tag));
   }
 
   int cslot = 0;
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
       for (int jj = 0; jj < a.n_in; ++jj)
         s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
              static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
-      hin = a.ain_g * s;
+      hin = df_from_double(a.ain_g * s);
     }
     for (int sub = 0; sub < a.S && !aborted; ++sub) {
       for (int st = 0; st < 4; ++st) {
@@ -487,40 +489,41 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
 
         // 3. torque, RK4 stage combination, publish the next stage's m^x
         if (owner) {
-          double dx, dy, dz;
-          llg_increment(a, msx, msy, msz, a.acp * static_cast<double>(hs[ctid]) + hin, dx, dy, dz);
-          if (st == 0) {
-            ax = dx; ay = dy; az = dz;
-            msx = mnx + 0.5 * dx; msy = mny + 0.5 * dy; msz = mnz + 0.5 * dz;
-          } else if (st == 1) {
-            ax += 2.0 * dx; ay += 2.0 * dy; az += 2.0 * dz;
-            msx = mnx + 0.5 * dx; msy = mny + 0.5 * dy; msz = mnz + 0.5 * dz;
-          } else if (st == 2) {
-            ax += 2.0 * dx; ay += 2.0 * dy; az += 2.0 * dz;
-            msx = mnx + dx; msy = mny + dy; msz = mnz + dz;
-          } else {
-            ax += dx; ay += dy; az += dz;
-            mnx += ax * (1.0 / 6.0); mny += ay * (1.0 / 6.0); mnz += az * (1.0 / 6.0);
-            msx = mnx; msy = mny; msz = mnz;
+          df d[3];
+          llg_increment(a, ms, df_add(df_mul_f(a.acp, hs[ctid]), hin), d);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            if (st == 0) {
+              ksum[i] = d[i];
+              ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
+            } else if (st == 1) {
+              ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
+              ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
+            } else if (st == 2) {
+              ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
+              ms[i] = df_add(mn[i], d[i]);
+            } else {
+              ksum[i] = df_add(ksum[i], d[i]);
+              mn[i] = df_add(mn[i], df_mul(ksum[i], a.sixth));
+              ms[i] = mn[i];
+            }
           }
           const unsigned nt = tag + 1u;
-          if (G == 1) xs[node] = static_cast<float>(msx);
+          if (G == 1) xs[node] = ms[0].hi;
           else if (publish)
-            st_relaxed_u64(a.xbuf + static_cast<size_t>(nt & 1u) * a.N + node,
-                           pack_x(static_cast<float>(msx), nt));
+            st_relaxed_u64(a.xbuf + static_cast<size_t>(nt & 1u) * a.N + node, pack_x(ms[0].hi, nt));
         }
         ++tag;
       }
     }
     if (!aborted && owner && a.states_out) {
-      const double v = a.comp == 0 ? mnx : (a.comp == 1 ? mny : mnz);
-      a.states_out[static_cast<size_t>(t) * a.N + node] = static_cast<float>(v);
+      const df v = a.comp == 0 ? mn[0] : (a.comp == 1 ? mn[1] : mn[2]);
+      a.states_out[static_cast<size_t>(t) * a.N + node] = v.hi;
     }
   }
   if (!aborted && owner) {
-    a.state[node] = mnx;
-    a.state[a.N + node] = mny;
-    a.state[2 * a.N + node] = mnz;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.state[static_cast<size_t>(i) * a.N + node] = df_to_double(mn[i]);
   }
 }
 
