@@ -35,10 +35,10 @@
 namespace sto {
 
 constexpr int kPanelCols = 128;                 // W columns per panel: 1 float4 per lane
-constexpr int kConsWarps = 16;                  // warps that consume panels
+constexpr int kConsWarps = 15;                  // warps that consume panels (16 warps in all: 128 registers each)
 constexpr int kCons = kConsWarps * 32;          // consumer threads
 constexpr int kThreads = kCons + 32;            // + one producer warp
-constexpr int kMaxRowsPerWarp = 16;             // rows of a CTA <= 256
+constexpr int kMaxRowsPerWarp = 16;             // rows of a CTA <= 240
 
 // Error word layout (int32[4]): code, CTA, stage tag, site.
 enum ErrSite { kSiteGather = 1, kSiteFull = 2, kSiteEmpty = 3, kSiteDrain = 4 };
@@ -53,6 +53,7 @@ struct KArgs {
   unsigned long long* xbuf;  // 2 x N tagged words
   int* err;                  // int32[4]
   int N, n_in, T, S, P, ns, resident, comp, inject_cta;
+  int l2_keep;               // W small enough to stay in L2 between stages
   unsigned int tag_base;
   unsigned long long timeout_ns;
   // constants of Eq. (gov) as double-float pairs
@@ -184,69 +185,83 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Spin on one tagged word until it carries `tag`; false on timeout or when
-// any CTA has recorded an error.
-__device__ __noinline__ bool poll_word(const unsigned long long* p, unsigned tag,
-                                       const KArgs& a, unsigned long long* out) {
+// Spin on one tagged word until it carries `tag`.  Returns the word, or 0
+// (tag 0 is never used) after a timeout or when any CTA has recorded an error.
+__device__ __noinline__ unsigned long long poll_word(const unsigned long long* p, unsigned tag,
+                                                     int* err, unsigned long long timeout_ns) {
   const unsigned long long t0 = gtimer();
   for (uint32_t n = 1;; ++n) {
-    unsigned long long w = ld_relaxed_u64(p);
-    if (static_cast<unsigned>(w >> 32) == tag) {
-      *out = w;
-      return true;
-    }
+    const unsigned long long w = ld_relaxed_u64(p);
+    if (static_cast<unsigned>(w >> 32) == tag) return w;
     if ((n & 31u) == 0) {
-      if (ld_relaxed_i32(a.err) != 0) return false;
-      if (gtimer() - t0 > a.timeout_ns) {
-        report_error(a.err, kErrTimeout, blockIdx.x, tag, kSiteGather);
-        return false;
+      if (ld_relaxed_i32(err) != 0) return 0ull;
+      if (gtimer() - t0 > timeout_ns) {
+        report_error(err, kErrTimeout, blockIdx.x, tag, kSiteGather);
+        return 0ull;
       }
     }
   }
 }
 
-// Copy the stage's m^x (tag) of all N oscillators into xs.
-__device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag, int ctid) {
+// Copy the stage's m^x (tag) of all N oscillators into xs; thread `g` of
+// `ng` gatherers takes words g, g + ng, ...
+__device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag, int g, int ng) {
   const unsigned long long* xb = a.xbuf + static_cast<size_t>(tag & 1u) * a.N;
-  for (int base = ctid; base < a.N; base += 4 * kCons) {
+  for (int base = g; base < a.N; base += 4 * ng) {
     unsigned long long w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int i = base + q * kCons;
+      const int i = base + q * ng;
       w[q] = (i < a.N) ? ld_relaxed_u64(xb + i) : 0ull;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int i = base + q * kCons;
+      const int i = base + q * ng;
       if (i < a.N) {
-        if (static_cast<unsigned>(w[q] >> 32) != tag && !poll_word(xb + i, tag, a, &w[q]))
-          return false;
-        xs[i] = __uint_as_float(static_cast<unsigned>(w[q]));
+        unsigned long long v = w[q];
+        if (static_cast<unsigned>(v >> 32) != tag) {
+          v = poll_word(xb + i, tag, a.err, a.timeout_ns);
+          if (v == 0ull) return false;
+        }
+        xs[i] = __uint_as_float(static_cast<unsigned>(v));
       }
     }
   }
   return true;
 }
 
-// dt * dm/dt of Eq. (gov) for one oscillator, in double-float.
-// hx = coupling + input field along e_x (Eq. coup + Eq. in).
-__device__ __forceinline__ void llg_increment(const KArgs& a, const df m[3], df hx, df d[3]) {
+// Eq. (gov) is affine in the x-field that coupling and input add to b:
+// with b = b0 + h e_x,
+//   dt dm/dt = -gamma' dt [m x b + alpha m x (m x b)] = A(m) + h B(m),
+//   A = -gamma' dt [m x b0 + alpha m x (m x b0)],
+//   B = -gamma' dt [m x e_x + alpha m x (m x e_x)]
+//     = -gamma' dt [(0, m_z, -m_y) + alpha (-(m_y^2 + m_z^2), m_x m_y, m_x m_z)],
+// where b0 = H(m) + H_s(m) p x m holds the anisotropy, applied and
+// spin-torque fields.  A and B depend only on the stage state, so they are
+// formed while the CTA waits for the other oscillators' m^x; once the
+// coupling field is known the increment costs three df multiply-adds.
+__device__ __forceinline__ void llg_affine(const KArgs& a, const df m[3], df A[3], df B[3]) {
   const df s = df_add(df_add(df_mul(m[0], a.px), df_mul(m[1], a.py)), df_mul(m[2], a.pz));  // m.p
   const df hs = df_mul(a.hs0, df_rcp(df_add_f(df_mul(a.lambda, s), 1.0f)));              // H_s(m)
   const df cx = df_cross1(a.py, m[2], a.pz, m[1]);                                          // p x m
   const df cy = df_cross1(a.pz, m[0], a.px, m[2]);
   const df cz = df_cross1(a.px, m[1], a.py, m[0]);
-  const df b[3] = {df_add(hx, df_mul(hs, cx)),                                              // b
-                   df_mul(hs, cy),
+  const df b[3] = {df_mul(hs, cx), df_mul(hs, cy),                                          // b0
                    df_add(df_add(a.happl, df_mul(a.hkp, m[2])), df_mul(hs, cz))};
-  const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]),                                       // m x b
+  const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]),                                       // m x b0
                    df_cross1(m[2], b[0], m[0], b[2]),
                    df_cross1(m[0], b[1], m[1], b[0])};
-  const df u[3] = {df_cross1(m[1], t[2], m[2], t[1]),                                       // m x (m x b)
+  const df u[3] = {df_cross1(m[1], t[2], m[2], t[1]),                                       // m x (m x b0)
                    df_cross1(m[2], t[0], m[0], t[2]),
                    df_cross1(m[0], t[1], m[1], t[0])};
+  const df e[3] = {df{0.f, 0.f}, m[2], df_neg(m[1])};                                       // m x e_x
+  const df v[3] = {df_neg(df_add(df_mul(m[1], m[1]), df_mul(m[2], m[2]))),                 // m x (m x e_x)
+                   df_mul(m[0], m[1]), df_mul(m[0], m[2])};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) d[i] = df_mul(a.gdt, df_add(t[i], df_mul(a.alpha, u[i])));  // -gamma' dt (...)
+  for (int i = 0; i < 3; ++i) {
+    A[i] = df_mul(a.gdt, df_add(t[i], df_mul(a.alpha, u[i])));
+    B[i] = df_mul(a.gdt, df_add(e[i], df_mul(a.alpha, v[i])));
+  }
 }
 
 // ------------------------------------------------------------ the stepper
@@ -297,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   // ------------------------------------------------------------ producer
   if constexpr (kRowMajorW) {
     if (warp == kConsWarps) {
-      const uint64_t pol = a.resident ? policy_evict_last() : policy_evict_first();
+      const uint64_t pol = (a.resident || a.l2_keep) ? policy_evict_last() : policy_evict_first();
       const long long total =
           a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
       const float* Wrows = a.W + static_cast<size_t>(r0) * a.N;
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   }
   if (warp == kConsWarps) {
     if (lane == 0) {
-      const uint64_t pol = a.resident ? policy_evict_last() : policy_evict_first();
+      const uint64_t pol = (a.resident || a.l2_keep) ? policy_evict_last() : policy_evict_first();
       const long long total =
           a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
       long long it = 0;
@@ -395,8 +410,12 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   const int node = r0 + ctid;
   const bool owner = ctid < R;
   const bool publish = (G > 1) && (c != a.inject_cta);
-  // state of the owned oscillator in double-float: m_n, stage state, RK4 sum
-  df mn[3], ms[3], ksum[3], hin = {0.f, 0.f};
+  // state of the owned oscillator in double-float: m_n, stage state, RK4 sum,
+  // and the affine parts A, B of the next increment
+  df mn[3], ms[3], ksum[3], fa[3], fb[3], hin = {0.f, 0.f};
+  // owners sit in the first warps; the others gather while owners form A, B
+  const int owner_warps = (R_max + 31) / 32;
+  const int gather_first = owner_warps < kConsWarps ? owner_warps * 32 : 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     mn[i] = owner ? df_from_double(a.state[static_cast<size_t>(i) * a.N + node]) : df{0.f, 0.f};
@@ -408,11 +427,24 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
     if (G == 1) xs[node] = ms[0].hi;
     else if (publish)
       st_relaxed_u64(a.xbuf + static_cast<size_t>(tag & 1u) * a.N + node, pack_x(ms[0].hi, tag));
+    llg_affine(a, ms, fa, fb);
   }
 
   int cslot = 0;
   uint32_t cphase = 0;
   bool aborted = false;
+  if (a.resident) {
+    // The row block is loaded once: wait for every panel here, not per stage.
+    bool landed = true;
+    for (int j = 0; j < a.P && landed; ++j)
+      landed = mbar_wait_bounded(&full[j], 0u, a.timeout_ns, s_abort);
+    landed = __all_sync(0xffffffffu, landed);
+    if (!landed && lane == 0) {
+      if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
+      *s_abort = 1;
+    }
+    aborted = consumer_sync_or(!landed);
+  }
   for (int t = 0; t < a.T && !aborted; ++t) {
     if (owner) {
       double s = 0.0;
@@ -425,7 +457,8 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
       for (int st = 0; st < 4; ++st) {
         // 1. the stage's m^x of every oscillator
         bool fail = false;
-        if (G > 1 && !gather_x(a, xs, tag, ctid)) {
+        if (G > 1 && ctid >= gather_first &&
+            !gather_x(a, xs, tag, ctid - gather_first, kCons - gather_first)) {
           fail = true;
           *s_abort = 1;
         }
@@ -435,36 +468,80 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
         float acc[RPW];
 #pragma unroll
         for (int qq = 0; qq < RPW; ++qq) acc[qq] = 0.f;
-        for (int j = 0; j < a.P; ++j) {
-          const int slot = a.resident ? j : cslot;
-          const uint32_t par = a.resident ? 0u : cphase;
-          // every lane waits; the vote keeps the warp's decision uniform
-          const bool landed = mbar_wait_bounded(&full[slot], par, a.timeout_ns, s_abort);
-          if (!__all_sync(0xffffffffu, landed)) {
-            if (lane == 0) {
-              if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
-              *s_abort = 1;
+        const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
+        if (a.resident) {
+          // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
+          // with few rows per warp, four partial sums per row shorten the
+          // dependent FMA chain
+          constexpr int kPart = RPW <= 2 ? 4 : 1;
+          float part[RPW][kPart];
+#pragma unroll
+          for (int qq = 0; qq < RPW; ++qq)
+#pragma unroll
+            for (int k = 0; k < kPart; ++k) part[qq][k] = 0.f;
+          const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
+          const int pstride = static_cast<int>(slot_floats / 4);
+#pragma unroll 4
+          for (int j = 0; j < a.P; ++j) {
+            const float4 xv = x4[j * (kPanelCols / 4)];
+            const float4* pj = w4 + j * pstride;
+#pragma unroll
+            for (int qq = 0; qq < RPW; ++qq) {
+              const int r = warp + qq * kConsWarps;
+              if (r < R) {
+                const float4 w = pj[r * (kPanelCols / 4)];
+                if constexpr (kPart == 4) {
+                  part[qq][0] = fmaf(w.x, xv.x, part[qq][0]);
+                  part[qq][1] = fmaf(w.y, xv.y, part[qq][1]);
+                  part[qq][2] = fmaf(w.z, xv.z, part[qq][2]);
+                  part[qq][3] = fmaf(w.w, xv.w, part[qq][3]);
+                } else {
+                  float v = part[qq][0];
+                  v = fmaf(w.x, xv.x, v);
+                  v = fmaf(w.y, xv.y, v);
+                  v = fmaf(w.z, xv.z, v);
+                  v = fmaf(w.w, xv.w, v);
+                  part[qq][0] = v;
+                }
+              }
             }
-            fail = true;
-            break;
           }
-          const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
-          const float4 xv = reinterpret_cast<const float4*>(xs)[j * (kPanelCols / 4) + lane];
 #pragma unroll
           for (int qq = 0; qq < RPW; ++qq) {
-            const int r = warp + qq * kConsWarps;
-            if (r < R) {
-              const float4 w = p4[r * (kPanelCols / 4) + lane];
-              float v = acc[qq];
-              v = fmaf(w.x, xv.x, v);
-              v = fmaf(w.y, xv.y, v);
-              v = fmaf(w.z, xv.z, v);
-              v = fmaf(w.w, xv.w, v);
-              acc[qq] = v;
-            }
+            if constexpr (kPart == 4)
+              acc[qq] = (part[qq][0] + part[qq][1]) + (part[qq][2] + part[qq][3]);
+            else
+              acc[qq] = part[qq][0];
           }
-          __syncwarp();
-          if (!a.resident) {
+        } else {
+          for (int j = 0; j < a.P; ++j) {
+            const int slot = cslot;
+            // every lane waits; the vote keeps the warp's decision uniform
+            const bool landed = mbar_wait_bounded(&full[slot], cphase, a.timeout_ns, s_abort);
+            if (!__all_sync(0xffffffffu, landed)) {
+              if (lane == 0) {
+                if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
+                *s_abort = 1;
+              }
+              fail = true;
+              break;
+            }
+            const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
+            const float4 xv = x4[j * (kPanelCols / 4)];
+#pragma unroll
+            for (int qq = 0; qq < RPW; ++qq) {
+              const int r = warp + qq * kConsWarps;
+              if (r < R) {
+                const float4 w = p4[r * (kPanelCols / 4) + lane];
+                float v = acc[qq];
+                v = fmaf(w.x, xv.x, v);
+                v = fmaf(w.y, xv.y, v);
+                v = fmaf(w.z, xv.z, v);
+                v = fmaf(w.w, xv.w, v);
+                acc[qq] = v;
+              }
+            }
+            __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
             if (++cslot == a.ns) {
               cslot = 0;
@@ -472,25 +549,28 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
             }
           }
         }
+        // butterfly sums of all rows at once (rows past R hold 0), so the
+        // shuffle chains of different rows overlap
 #pragma unroll
-        for (int qq = 0; qq < RPW; ++qq) {
-          const int r = warp + qq * kConsWarps;
-          if (r < R) {
-            float v = acc[qq];
-            v += __shfl_xor_sync(0xffffffffu, v, 16);
-            v += __shfl_xor_sync(0xffffffffu, v, 8);
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            if (lane == 0) hs[r] = v;
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+          for (int qq = 0; qq < RPW; ++qq) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], off);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int qq = 0; qq < RPW; ++qq) {
+            const int r = warp + qq * kConsWarps;
+            if (r < R) hs[r] = acc[qq];
           }
         }
         if (consumer_sync_or(fail)) { aborted = true; break; }
 
         // 3. torque, RK4 stage combination, publish the next stage's m^x
         if (owner) {
+          const df hx = df_add(df_mul_f(a.acp, hs[ctid]), hin);
           df d[3];
-          llg_increment(a, ms, df_add(df_mul_f(a.acp, hs[ctid]), hin), d);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) d[i] = df_add(fa[i], df_mul(hx, fb[i]));
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             if (st == 0) {
@@ -512,6 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
           if (G == 1) xs[node] = ms[0].hi;
           else if (publish)
             st_relaxed_u64(a.xbuf + static_cast<size_t>(nt & 1u) * a.N + node, pack_x(ms[0].hi, nt));
+          llg_affine(a, ms, fa, fb);  // for the next stage, overlapping the exchange
         }
         ++tag;
       }
