@@ -16,6 +16,9 @@ Parity status of each function (the pins are in ``tests/test_oracle_pins.py``):
                  closed-form trajectories, norm drift O(dt^4)
   initial_state  pinned: Eq. (initial) unit norm and the stated limit (0,0,1)
   readout        pinned: ridge at beta -> 0 equals numpy lstsq
+  adjoint        pinned: central finite differences of `run` (FP64) for A_cp,
+                 I, w_in and m0, including the refitted-readout objective
+                 (tests/test_oracle_adjoint.py)
 """
 from __future__ import annotations
 
@@ -121,6 +124,9 @@ def _load():
             lib.orc_run.restype = ctypes.c_int
             lib.orc_initial_state.argtypes = [ctypes.c_int, D]
             lib.orc_max_threads.restype = ctypes.c_int
+            lib.orc_adjoint.argtypes = [ctypes.c_int, P, D, D, D, D, ctypes.c_int, D, D,
+                                        ctypes.c_int]
+            lib.orc_adjoint.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -224,3 +230,28 @@ def run(params: OracleParams, W, w_in, m0, u, T: int | None = None, nthreads: in
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return m, states[:T]
+
+
+def adjoint(params: OracleParams, W, w_in, m0, u, dL_dstates, nthreads: int = 1) -> dict:
+    """Exact gradients of L = sum(dL_dstates * states) for one run from m0
+    (discrete adjoint of the RK4 stepper).  Returns dA_cp, dI, dw_in (N, n_in)
+    and dm0 (3, N)."""
+    W = _f64(W)
+    N = W.shape[0]
+    u = _f64(u)
+    if u.ndim == 1:
+        u = u.reshape(-1, 1)
+    T = u.shape[0]
+    u = np.ascontiguousarray(u.reshape(T, params.n_in))
+    w_in = _f64(w_in).reshape(N, params.n_in)
+    m0 = _f64(m0, (3, N))
+    g = _f64(dL_dstates, (T, N))
+    out = np.zeros(2 + N * params.n_in + 3 * N)
+    c = params._c()
+    rc = _load().orc_adjoint(N, ctypes.byref(c), _d(W), _d(w_in), _d(m0), _d(u), T, _d(g),
+                             _d(out), nthreads)
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    nw = N * params.n_in
+    return {"A_cp": out[0], "current": out[1], "w_in": out[2:2 + nw].reshape(N, params.n_in),
+            "m0": out[2 + nw:].reshape(3, N)}

@@ -215,3 +215,173 @@ int orc_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of the RK4 stepper (gradients of a scalar loss that
+ * depends on the sampled states).  Not part of the paper's method: it is the
+ * reference for the gradient-based parameter search built on top of it
+ * (Sec. 1 and Sec. 2 call the parameter exploration time-consuming).
+ *
+ * Given dL/dstates (T x N), computes the exact derivatives of
+ *     L = sum_t sum_k dL_dstates[t,k] * states[t,k]
+ * (a vector-Jacobian product of the whole run) with respect to
+ *     A_cp, the current I, w_in (N x n_in) and the initial state m0 (3N).
+ * RK4 step m' = m + dt/6 (k1 + 2 k2 + 2 k3 + k4), k_s = f(y_s):
+ *     kb4 = dt/6 lam;           yb4 = J(y4)^T kb4
+ *     kb3 = dt/3 lam + dt yb4;  yb3 = J(y3)^T kb3
+ *     kb2 = dt/3 lam + dt/2 yb3; yb2 = J(y2)^T kb2
+ *     kb1 = dt/6 lam + dt/2 yb2; yb1 = J(y1)^T kb1
+ *     lam <- lam + yb1 + yb2 + yb3 + yb4,
+ * and each J^T kb also yields the parameter terms (kb . df/dtheta at y_s).
+ * J^T v for one oscillator, with b the full field at m:
+ *     bbar = gamma' (m x v) - alpha gamma' m x (m x v)          (d/db)
+ *     mbar = -gamma' [b x v + alpha ((m.b) v + (m.v) b - 2 (b.v) m)]
+ *            + H_K' bbar_z e_z + H_s (bbar x p) - (bbar.c) lambda H_s/(1+lambda s) p
+ *     coupling: xbar_i += A_cp sum_k W[k,i] bbar_x,k
+ * ------------------------------------------------------------------------ */
+
+/* J^T v for all oscillators at state y (3N) with input field hin; adds the
+ * state cotangent into ybar (3N) and the parameter terms into g. */
+static void orc_field_vjp(int N, const orc_params* P, const double d[3], const double* W,
+                          const double* w_in, const double* u_t, const double* y,
+                          const double* hin, const double* v, double* ybar, double* gA,
+                          double* gI, double* gwin, int nthreads) {
+  const double gp = d[0], HKp = d[1], Hs0 = d[2];
+  const double dHs0_dI = P->hbar * P->eta * 1.0e7 / (2.0 * P->e * P->M * P->V);
+  const double* p = P->p;
+  double* hraw = (double*)malloc(sizeof(double) * (size_t)N);
+  double* gbar = (double*)malloc(sizeof(double) * (size_t)N);
+  orc_params Pone = *P;
+  Pone.A_cp = 1.0;
+  orc_coupling(N, &Pone, W, y, hraw, nthreads); /* raw W x */
+  for (int k = 0; k < N; ++k) {
+    double m[3] = {y[k], y[N + k], y[2 * N + k]};
+    double vv[3] = {v[k], v[N + k], v[2 * N + k]};
+    double s = m[0] * p[0] + m[1] * p[1] + m[2] * p[2];
+    double D = 1.0 + P->lambda * s;
+    double Hs = Hs0 / D;
+    double c[3] = {p[1] * m[2] - p[2] * m[1], p[2] * m[0] - p[0] * m[2],
+                   p[0] * m[1] - p[1] * m[0]};
+    double b[3] = {P->A_cp * hraw[k] + hin[k] + Hs * c[0], Hs * c[1],
+                   P->H_appl + HKp * m[2] + Hs * c[2]};
+    /* bbar = gamma' (m x v) - alpha gamma' m x (m x v) */
+    double mv[3] = {m[1] * vv[2] - m[2] * vv[1], m[2] * vv[0] - m[0] * vv[2],
+                    m[0] * vv[1] - m[1] * vv[0]};
+    double mmv[3] = {m[1] * mv[2] - m[2] * mv[1], m[2] * mv[0] - m[0] * mv[2],
+                     m[0] * mv[1] - m[1] * mv[0]};
+    double bb[3];
+    for (int a = 0; a < 3; ++a) bb[a] = gp * mv[a] - P->alpha * gp * mmv[a];
+    /* explicit m dependence at fixed b */
+    double bxv[3] = {b[1] * vv[2] - b[2] * vv[1], b[2] * vv[0] - b[0] * vv[2],
+                     b[0] * vv[1] - b[1] * vv[0]};
+    double mb = m[0] * b[0] + m[1] * b[1] + m[2] * b[2];
+    double mvd = m[0] * vv[0] + m[1] * vv[1] + m[2] * vv[2];
+    double bv = b[0] * vv[0] + b[1] * vv[1] + b[2] * vv[2];
+    double mbar[3];
+    for (int a = 0; a < 3; ++a)
+      mbar[a] = -gp * (bxv[a] + P->alpha * (mb * vv[a] + mvd * b[a] - 2.0 * bv * m[a]));
+    /* through b(m): anisotropy and spin torque */
+    mbar[2] += HKp * bb[2];
+    double bbxp[3] = {bb[1] * p[2] - bb[2] * p[1], bb[2] * p[0] - bb[0] * p[2],
+                      bb[0] * p[1] - bb[1] * p[0]};
+    double bc = bb[0] * c[0] + bb[1] * c[1] + bb[2] * c[2];
+    for (int a = 0; a < 3; ++a) mbar[a] += Hs * bbxp[a] - bc * P->lambda * Hs / D * p[a];
+    ybar[k] += mbar[0];
+    ybar[N + k] += mbar[1];
+    ybar[2 * N + k] += mbar[2];
+    gbar[k] = bb[0];
+    /* parameters */
+    *gA += bb[0] * hraw[k];
+    *gI += bc * dHs0_dI / D;
+    for (int j = 0; j < P->n_in; ++j)
+      gwin[(size_t)k * P->n_in + j] += bb[0] * P->g * P->A_in * u_t[j];
+  }
+  /* coupling: xbar_i += A_cp sum_k W[k,i] gbar_k (column sums, ascending k) */
+  for (int i = 0; i < N; ++i) {
+    double sacc = 0.0;
+    for (int k = 0; k < N; ++k) sacc += W[(size_t)k * N + i] * gbar[k];
+    ybar[i] += P->A_cp * sacc;
+  }
+  free(hraw);
+  free(gbar);
+}
+
+/* grads layout: [0] dL/dA_cp, [1] dL/dI, [2 .. 2 + N n_in) dL/dw_in,
+ * then 3N entries dL/dm0.  Returns 0, or -1 on bad arguments. */
+int orc_adjoint(int N, const orc_params* P, const double* W, const double* w_in,
+                const double* m0, const double* u, int T, const double* dL_dstates,
+                double* grads, int nthreads) {
+  if (N < 1 || T < 1 || !P || !W || !w_in || !m0 || !u || !dL_dstates || !grads ||
+      P->substeps < 1 || P->n_in < 1 || P->component < 0 || P->component > 2)
+    return -1;
+  const int S = P->substeps;
+  const size_t n3 = 3 * (size_t)N;
+  const long long steps = (long long)T * S;
+  double d[3];
+  orc_derived(P, d);
+  /* forward, keeping the state before every RK4 step */
+  double* traj = (double*)malloc(sizeof(double) * n3 * (size_t)(steps + 1));
+  double* hin = (double*)malloc(sizeof(double) * (size_t)N);
+  memcpy(traj, m0, sizeof(double) * n3);
+  for (int t = 0; t < T; ++t) {
+    orc_input_field(N, P, w_in, u + (size_t)t * P->n_in, hin);
+    for (int s = 0; s < S; ++s) {
+      long long n = (long long)t * S + s;
+      memcpy(traj + n3 * (size_t)(n + 1), traj + n3 * (size_t)n, sizeof(double) * n3);
+      orc_rk4_step(N, P, W, hin, traj + n3 * (size_t)(n + 1), nthreads);
+    }
+  }
+  /* reverse sweep */
+  const size_t nwin = (size_t)N * P->n_in;
+  double gA = 0.0, gI = 0.0;
+  double* gwin = (double*)calloc(nwin, sizeof(double));
+  double* lam = (double*)calloc(n3, sizeof(double));
+  double* y = (double*)malloc(sizeof(double) * n3);
+  double* k1 = (double*)malloc(sizeof(double) * n3);
+  double* k2 = (double*)malloc(sizeof(double) * n3);
+  double* k3 = (double*)malloc(sizeof(double) * n3);
+  double* y2 = (double*)malloc(sizeof(double) * n3);
+  double* y3 = (double*)malloc(sizeof(double) * n3);
+  double* y4 = (double*)malloc(sizeof(double) * n3);
+  double* kb = (double*)malloc(sizeof(double) * n3);
+  double* yb[4];
+  for (int q = 0; q < 4; ++q) yb[q] = (double*)malloc(sizeof(double) * n3);
+  const double dt = P->dt;
+  for (long long n = steps - 1; n >= 0; --n) {
+    const int t = (int)(n / S);
+    if (n % S == S - 1)  /* the state after this step is sample t */
+      for (int k = 0; k < N; ++k)
+        lam[(size_t)P->component * N + k] += dL_dstates[(size_t)t * N + k];
+    const double* u_t = u + (size_t)t * P->n_in;
+    orc_input_field(N, P, w_in, u_t, hin);
+    const double* m = traj + n3 * (size_t)n;
+    /* stage points */
+    orc_field(N, P, W, m, hin, k1, NULL, nthreads);
+    for (size_t a = 0; a < n3; ++a) y2[a] = m[a] + 0.5 * dt * k1[a];
+    orc_field(N, P, W, y2, hin, k2, NULL, nthreads);
+    for (size_t a = 0; a < n3; ++a) y3[a] = m[a] + 0.5 * dt * k2[a];
+    orc_field(N, P, W, y3, hin, k3, NULL, nthreads);
+    for (size_t a = 0; a < n3; ++a) y4[a] = m[a] + dt * k3[a];
+    /* stage 4 */
+    for (size_t a = 0; a < n3; ++a) { kb[a] = dt / 6.0 * lam[a]; yb[3][a] = 0.0; }
+    orc_field_vjp(N, P, d, W, w_in, u_t, y4, hin, kb, yb[3], &gA, &gI, gwin, nthreads);
+    /* stage 3 */
+    for (size_t a = 0; a < n3; ++a) { kb[a] = dt / 3.0 * lam[a] + dt * yb[3][a]; yb[2][a] = 0.0; }
+    orc_field_vjp(N, P, d, W, w_in, u_t, y3, hin, kb, yb[2], &gA, &gI, gwin, nthreads);
+    /* stage 2 */
+    for (size_t a = 0; a < n3; ++a) { kb[a] = dt / 3.0 * lam[a] + 0.5 * dt * yb[2][a]; yb[1][a] = 0.0; }
+    orc_field_vjp(N, P, d, W, w_in, u_t, y2, hin, kb, yb[1], &gA, &gI, gwin, nthreads);
+    /* stage 1 */
+    for (size_t a = 0; a < n3; ++a) { kb[a] = dt / 6.0 * lam[a] + 0.5 * dt * yb[1][a]; yb[0][a] = 0.0; }
+    orc_field_vjp(N, P, d, W, w_in, u_t, m, hin, kb, yb[0], &gA, &gI, gwin, nthreads);
+    for (size_t a = 0; a < n3; ++a) lam[a] += yb[0][a] + yb[1][a] + yb[2][a] + yb[3][a];
+  }
+  grads[0] = gA;
+  grads[1] = gI;
+  memcpy(grads + 2, gwin, sizeof(double) * nwin);
+  memcpy(grads + 2 + nwin, lam, sizeof(double) * n3);
+  free(traj); free(hin); free(gwin); free(lam); free(y); free(k1); free(k2); free(k3);
+  free(y2); free(y3); free(y4); free(kb);
+  for (int q = 0; q < 4; ++q) free(yb[q]);
+  return 0;
+}
