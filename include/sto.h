@@ -177,6 +177,43 @@ STO_API int sto_get_state_f64(const sto_handle* h, double* m);
  *         larger than any earlier call need a device staging buffer). */
 STO_API int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out);
 
+/* Gradients returned by sto_adjoint. */
+typedef struct sto_grads {
+  double dA_cp;      /* dL/dA_cp */
+  double dcurrent;   /* dL/dI (per ampere) */
+  double* dw_in;     /* N x n_in output, host or device, or NULL */
+  double* dm0;       /* 3 x N output (dL/dm at the start), host or device, or NULL */
+} sto_grads;
+
+/* Gradients for parameter search (Sec. 1 and Sec. 2 call the exploration of
+ * the parameter space the time-consuming part): the exact derivatives of
+ *     L = sum_{t,k} dL_dstates[t*N + k] * states_out[t*N + k]
+ * for the run sto_run(h, u, T, states_out) would do from the current state,
+ * with respect to A_cp, the current I, the input weights w_in and the
+ * initial state.  This is the discrete adjoint of the RK4 stepper (not an
+ * adjoint ODE), so it matches finite differences of sto_run to rounding.
+ * With dL_dstates = dLoss/dstates of a readout loss evaluated at the fitted
+ * readout weights, the result is the gradient of the refitted loss
+ * (envelope theorem).
+ *   u, T          as for sto_run (T >= 1).
+ *   dL_dstates    T x N float32, host or device.
+ *   ckpt_every    K >= 1: the state is checkpointed every K input samples;
+ *                 each K-sample segment is recomputed once with its
+ *                 trajectory recorded (K * substeps * N * 40 bytes of device
+ *                 memory), then swept backwards.  Cost: about three forward
+ *                 runs plus one reverse run with a W^T product per stage.
+ *   out           receives dA_cp and dcurrent; dw_in / dm0 are written if
+ *                 non-NULL.
+ * The state ends where sto_run would leave it.  The first call builds a
+ * tiled copy of W^T (another 4 N^2 bytes).
+ * Errors: STO_EINVAL, STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA, STO_ENOTSUP. */
+STO_API int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstates,
+                        int32_t ckpt_every, sto_grads* out);
+
+/* Replace the input weights w_in (N x n_in float32, host or device).
+ * Errors: STO_EINVAL, STO_ENONFINITE, STO_ECUDA. */
+STO_API int sto_set_input_weights(sto_handle* h, const float* w_in);
+
 /* Report the launch plan. */
 STO_API int sto_get_info(const sto_handle* h, sto_info* out);
 

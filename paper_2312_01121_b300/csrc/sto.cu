@@ -162,6 +162,16 @@ struct sto_handle {
   size_t d_u_cap = 0;
   float* d_states = nullptr;
   size_t d_states_cap = 0;
+  // adjoint working set (allocated on the first sto_adjoint)
+  float* d_WT = nullptr;       // W^T in the tiled layout of the plan
+  float* d_rec = nullptr;      // recording of one segment (rec_m then rec_h)
+  size_t d_rec_cap = 0;        // floats
+  double* d_ckpt = nullptr;    // checkpoints, (segments + 1) x 3N
+  size_t d_ckpt_cap = 0;       // doubles
+  double* d_lam = nullptr;     // 3N
+  double* d_gacc = nullptr;    // g_acp (N) | g_cur (N) | g_win (N n_in)
+  float* d_dl = nullptr;       // staged dL/dstates
+  size_t d_dl_cap = 0;
 };
 
 namespace {
@@ -175,13 +185,19 @@ void free_handle(sto_handle* h) {
   cudaFree(h->d_err);
   cudaFree(h->d_u);
   cudaFree(h->d_states);
+  cudaFree(h->d_WT);
+  cudaFree(h->d_rec);
+  cudaFree(h->d_ckpt);
+  cudaFree(h->d_lam);
+  cudaFree(h->d_gacc);
+  cudaFree(h->d_dl);
   if (h->h_err) cudaFreeHost(h->h_err);
   delete h;
 }
 
-template <int RPW, bool kRowMajorW = false>
+template <int RPW, bool kRowMajorW = false, bool kAdjoint = false>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW>,
+  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW, kAdjoint>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(pl.smem));
   if (e != cudaSuccess) return e;
@@ -195,7 +211,7 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kAdjoint>, a);
 }
 
 cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -204,6 +220,14 @@ cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStr
   if (pl.rpw <= 4) return launch_rpw<4, true>(pl, a, s);
   if (pl.rpw <= 8) return launch_rpw<8, true>(pl, a, s);
   return launch_rpw<16, true>(pl, a, s);
+}
+
+cudaError_t launch_adjoint(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  if (pl.rpw <= 1) return launch_rpw<1, false, true>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2, false, true>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4, false, true>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8, false, true>(pl, a, s);
+  return launch_rpw<16, false, true>(pl, a, s);
 }
 
 cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -288,6 +312,7 @@ void set_constants(const sto_params& P, sto::KArgs* a) {
   a->acp = df_split_host(P.A_cp);
   a->sixth = df_split_host(1.0 / 6.0);
   a->ain_g = P.A_in * P.input_gain;
+  a->dhs0_di_f = static_cast<float>(P.hbar * P.eta * 1.0e7 / (2.0 * P.e_charge * P.Ms * P.volume));
 }
 
 // ------------------------------------------------- allocation-free entry point
@@ -317,6 +342,113 @@ int noalloc_scratch(int dev, unsigned char** out) {
     g_noalloc_dev[dev] = static_cast<unsigned char*>(p);
   }
   *out = g_noalloc_dev[dev];
+  return STO_OK;
+}
+
+int grow_d(double** buf, size_t* cap, size_t n) {
+  if (*cap >= n) return STO_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return STO_ENOMEM;
+  }
+  *cap = n;
+  return STO_OK;
+}
+
+// Kernel arguments shared by the forward and adjoint launches of a handle.
+sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
+  const sto_params& P = h->params;
+  sto::KArgs a{};
+  a.W = h->d_W;
+  a.w_in = h->d_win;
+  a.u = d_u;
+  a.state = h->d_state;
+  a.xbuf = h->d_xbuf;
+  a.err = h->d_err;
+  a.N = static_cast<int>(h->N);
+  a.n_in = P.n_in;
+  a.T = static_cast<int>(T);
+  a.S = P.substeps;
+  a.P = h->plan.P;
+  a.ns = h->plan.ns;
+  a.resident = h->plan.resident;
+  a.comp = P.sample_component;
+  a.inject_cta = h->inject_cta;
+  a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
+  a.l2_keep = l2_keeps(h->N);
+  set_constants(P, &a);
+  // tags [base, base + stages] are fresh: none was written before
+  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
+    cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(h->N) * 8, h->stream);
+    h->stage_counter = 0;
+  }
+  const uint64_t base = h->stage_counter + 1;
+  h->stage_counter = base + stages;
+  a.tag_base = static_cast<unsigned>(base);
+  return a;
+}
+
+// Enqueue one forward launch (optionally recording the trajectory).
+int engine_launch(sto_handle* h, const float* d_u, int64_t T, float* d_states,
+                  float2* rec_m, float* rec_h) {
+  sto::KArgs a = base_args(h, d_u, T);
+  a.states_out = d_states;
+  a.rec_m = rec_m;
+  a.rec_h = rec_h;
+  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, h->stream));
+  STO_CUDA(launch_stepper(h->plan, a, h->stream));
+  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, h->stream));
+  return STO_OK;
+}
+
+// Enqueue one adjoint launch over a recorded segment of T samples.
+int engine_launch_adjoint(sto_handle* h, const float* d_u, int64_t T, const float* d_dl,
+                          const float2* rec_m, const float* rec_h) {
+  sto::KArgs a = base_args(h, d_u, T);
+  a.W = h->d_WT;
+  a.rec_m = const_cast<float2*>(rec_m);
+  a.rec_h = const_cast<float*>(rec_h);
+  a.dLds = d_dl;
+  a.lam = h->d_lam;
+  a.g_acp = h->d_gacc;
+  a.g_cur = h->d_gacc + h->N;
+  a.g_win = h->d_gacc + 2 * h->N;
+  a.inject_cta = -1;
+  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, h->stream));
+  STO_CUDA(launch_adjoint(h->plan, a, h->stream));
+  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, h->stream));
+  return STO_OK;
+}
+
+// Wait for the enqueued launch and turn its error word into a status.
+int finish_launch(sto_handle* h) {
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  h->inject_cta = -1;
+  if (h->h_err[0] != 0) return h->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  return STO_OK;
+}
+
+// W^T in the tiled layout of the plan, derived from the tiled W.
+int ensure_transpose(sto_handle* h) {
+  if (h->d_WT) return STO_OK;
+  const size_t elems = static_cast<size_t>(h->N) * h->plan.P * sto::kPanelCols;
+  if (cudaMalloc(&h->d_WT, elems * 4) != cudaSuccess) {
+    cudaGetLastError();
+    h->d_WT = nullptr;
+    return STO_ENOMEM;
+  }
+  STO_CUDA(cudaMemsetAsync(h->d_WT, 0, elems * 4, h->stream));
+  long long blocks = (h->N * h->N + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  sto::transpose_tiled_kernel<<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
+      h->d_W, h->d_WT, static_cast<int>(h->N), h->plan.G, h->plan.P);
+  STO_CUDA(cudaGetLastError());
+  STO_CUDA(cudaStreamSynchronize(h->stream));
   return STO_OK;
 }
 
@@ -580,46 +712,115 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
     if (rc) return rc;
     d_states = h->d_states;
   }
-
-  // tags [base, base + stages] are fresh: none was written before
-  if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
-    STO_CUDA(cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(N) * 8, s));
-    h->stage_counter = 0;
-  }
-  const uint64_t base = h->stage_counter + 1;
-  h->stage_counter = base + stages;
-
-  sto::KArgs a{};
-  a.W = h->d_W;
-  a.w_in = h->d_win;
-  a.u = d_u;
-  a.state = h->d_state;
-  a.states_out = d_states;
-  a.xbuf = h->d_xbuf;
-  a.err = h->d_err;
-  a.N = static_cast<int>(N);
-  a.n_in = P.n_in;
-  a.T = static_cast<int>(T);
-  a.S = P.substeps;
-  a.P = h->plan.P;
-  a.ns = h->plan.ns;
-  a.resident = h->plan.resident;
-  a.comp = P.sample_component;
-  a.inject_cta = h->inject_cta;
-  a.tag_base = static_cast<unsigned>(base);
-  a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
-  a.l2_keep = l2_keeps(N);
-  set_constants(P, &a);
-
-  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
-  STO_CUDA(launch_stepper(h->plan, a, s));
-  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s));
+  const int rc = engine_launch(h, d_u, T, d_states, nullptr, nullptr);
+  if (rc) return rc;
   if (host_states)
     STO_CUDA(cudaMemcpyAsync(states_out, d_states, n_states * 4, cudaMemcpyDeviceToHost, s));
+  return finish_launch(h);
+}
+
+int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstates,
+                int32_t ckpt_every, sto_grads* out) {
+  if (!h || T < 1 || !u || !dL_dstates || !out || ckpt_every < 1) return STO_EINVAL;
+  const sto_params& P = h->params;
+  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
+  const int64_t N = h->N;
+  const int n_in = P.n_in;
+  cudaStream_t s = h->stream;
+  const int64_t K = ckpt_every < T ? ckpt_every : T;
+  const int64_t nseg = (T + K - 1) / K;
+  const size_t n3 = 3 * static_cast<size_t>(N);
+  const size_t rec_floats = static_cast<size_t>(K) * P.substeps * static_cast<size_t>(N) * 10;
+  int rc;
+
+  // inputs on the device
+  const float* d_u = u;
+  if (!is_device_ptr(u)) {
+    rc = grow(&h->d_u, &h->d_u_cap, static_cast<size_t>(T) * n_in);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(h->d_u, u, static_cast<size_t>(T) * n_in * 4, cudaMemcpyHostToDevice, s));
+    d_u = h->d_u;
+  }
+  const float* d_dl = dL_dstates;
+  if (!is_device_ptr(dL_dstates)) {
+    rc = grow(&h->d_dl, &h->d_dl_cap, static_cast<size_t>(T) * N);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(h->d_dl, dL_dstates, static_cast<size_t>(T) * N * 4,
+                             cudaMemcpyHostToDevice, s));
+    d_dl = h->d_dl;
+  }
+  // working set
+  rc = ensure_transpose(h);
+  if (rc) return rc;
+  rc = grow(&h->d_rec, &h->d_rec_cap, rec_floats);
+  if (rc) return rc;
+  rc = grow_d(&h->d_ckpt, &h->d_ckpt_cap, static_cast<size_t>(nseg + 1) * n3);
+  if (rc) return rc;
+  if (!h->d_lam) {
+    if (cudaMalloc(&h->d_lam, n3 * 8) != cudaSuccess ||
+        cudaMalloc(&h->d_gacc, (2 + static_cast<size_t>(n_in)) * N * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return STO_ENOMEM;
+    }
+  }
+  float2* rec_m = reinterpret_cast<float2*>(h->d_rec);
+  float* rec_h = h->d_rec + static_cast<size_t>(K) * P.substeps * N * 6;
+
+  // 1. checkpoints every K samples
+  STO_CUDA(cudaMemcpyAsync(h->d_ckpt, h->d_state, n3 * 8, cudaMemcpyDeviceToDevice, s));
+  for (int64_t g = 0; g < nseg; ++g) {
+    const int64_t t0 = g * K, Tg = (T - t0) < K ? (T - t0) : K;
+    rc = engine_launch(h, d_u + t0 * n_in, Tg, nullptr, nullptr, nullptr);
+    if (!rc) rc = finish_launch(h);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(h->d_ckpt + (g + 1) * n3, h->d_state, n3 * 8,
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  // 2. segments in reverse: recompute with recording, then the adjoint pass
+  STO_CUDA(cudaMemsetAsync(h->d_lam, 0, n3 * 8, s));
+  STO_CUDA(cudaMemsetAsync(h->d_gacc, 0, (2 + static_cast<size_t>(n_in)) * N * 8, s));
+  for (int64_t g = nseg - 1; g >= 0; --g) {
+    const int64_t t0 = g * K, Tg = (T - t0) < K ? (T - t0) : K;
+    STO_CUDA(cudaMemcpyAsync(h->d_state, h->d_ckpt + g * n3, n3 * 8, cudaMemcpyDeviceToDevice, s));
+    rc = engine_launch(h, d_u + t0 * n_in, Tg, nullptr, rec_m, rec_h);
+    if (!rc) rc = finish_launch(h);
+    if (!rc) rc = engine_launch_adjoint(h, d_u + t0 * n_in, Tg, d_dl + t0 * N, rec_m, rec_h);
+    if (!rc) rc = finish_launch(h);
+    if (rc) return rc;
+  }
+  // 3. results; the state ends where sto_run would leave it
+  STO_CUDA(cudaMemcpyAsync(h->d_state, h->d_ckpt + nseg * n3, n3 * 8, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> gacc((2 + static_cast<size_t>(n_in)) * N);
+  std::vector<double> lam(n3);
+  STO_CUDA(cudaMemcpyAsync(gacc.data(), h->d_gacc, gacc.size() * 8, cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaMemcpyAsync(lam.data(), h->d_lam, n3 * 8, cudaMemcpyDeviceToHost, s));
   STO_CUDA(cudaStreamSynchronize(s));
-  h->inject_cta = -1;
-  if (h->h_err[0] != 0) return h->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  double ga = 0.0, gc = 0.0;
+  for (int64_t k = 0; k < N; ++k) {
+    ga += gacc[k];
+    gc += gacc[N + k];
+  }
+  out->dA_cp = ga;
+  out->dcurrent = gc;
+  if (out->dw_in) {
+    STO_CUDA(cudaMemcpyAsync(out->dw_in, gacc.data() + 2 * N, static_cast<size_t>(N) * n_in * 8,
+                             cudaMemcpyDefault, s));
+  }
+  if (out->dm0) STO_CUDA(cudaMemcpyAsync(out->dm0, lam.data(), n3 * 8, cudaMemcpyDefault, s));
+  STO_CUDA(cudaStreamSynchronize(s));
   return STO_OK;
+}
+
+int sto_set_input_weights(sto_handle* h, const float* w_in) {
+  if (!h || !w_in) return STO_EINVAL;
+  const size_t n = static_cast<size_t>(h->N) * h->params.n_in;
+  int rc = upload_floats(h->d_win, w_in, n, h->stream);
+  if (rc) return rc;
+  bool bad = false;
+  rc = any_nonfinite(h->d_win, static_cast<long long>(n), h->stream, h->d_err, h->h_err, &bad);
+  if (rc) return rc;
+  return bad ? STO_ENONFINITE : STO_OK;
 }
 
 int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const float* w_in,

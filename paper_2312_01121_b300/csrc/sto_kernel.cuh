@@ -28,6 +28,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
@@ -60,6 +61,18 @@ struct KArgs {
   df gdt;        // -gamma' * dt
   df alpha, happl, hkp, hs0, lambda, px, py, pz, acp, sixth;
   double ain_g;  // g * A_in (input field formed once per sample in FP64)
+  // forward recording for the adjoint (nullptr: off): per RK4 step n the
+  // state before the step (rec_m[(n*3 + i)*N + k], df pairs) and the raw
+  // coupling sums of its four stages (rec_h[(n*4 + s)*N + k])
+  float2* rec_m;
+  float* rec_h;
+  // adjoint pass (kAdjoint kernels only)
+  const float* dLds;         // T x N: dL/dstates of the segment
+  double* lam;               // 3 x N: dL/dm at the segment end (in), at its start (out)
+  double* g_win;             // N x n_in accumulated dL/dw_in
+  double* g_acp;             // N partial sums of dL/dA_cp
+  double* g_cur;             // N partial sums of dL/dI
+  float dhs0_di_f;           // dH_s0/dI (the adjoint's dL/dI term)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -264,13 +277,309 @@ __device__ __forceinline__ void llg_affine(const KArgs& a, const df m[3], df A[3
   }
 }
 
+// ------------------------------------------------------- owner programs
+//
+// The engine below exchanges one float per oscillator per stage and reduces
+// W z for the published z.  What an oscillator's owner thread does with the
+// reduced sum, and what it publishes next, is its "program".
+
+// Publishes oscillator `node`'s stage value under tag `tg`.
+struct Publisher {
+  unsigned long long* xbuf;
+  float* xs;
+  int N;
+  bool single;   // one CTA: write shared memory directly
+  bool enabled;  // false only for the CTA a test stalls on purpose
+  __device__ __forceinline__ void operator()(int node, float v, unsigned tg) const {
+    if (single)
+      xs[node] = v;
+    else if (enabled)
+      st_relaxed_u64(xbuf + static_cast<size_t>(tg & 1u) * N + node, pack_x(v, tg));
+  }
+};
+
+// Forward RK4 (Sec. 3.2) of Eq. (gov): publishes m^x of every stage state.
+struct ForwardProgram {
+  df mn[3], ms[3], ksum[3], fa[3], fb[3], hin;
+  int t, sub;
+
+  __device__ __forceinline__ void load_hin(const KArgs& a, int node) {
+    double s = 0.0;
+    for (int jj = 0; jj < a.n_in; ++jj)
+      s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
+           static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
+    hin = df_from_double(a.ain_g * s);
+  }
+
+  __device__ __forceinline__ void init(const KArgs& a, int node, const Publisher& pub, unsigned tag) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      mn[i] = df_from_double(a.state[static_cast<size_t>(i) * a.N + node]);
+      ms[i] = mn[i];
+      ksum[i] = df{0.f, 0.f};
+    }
+    t = 0;
+    sub = 0;
+    load_hin(a, node);
+    pub(node, ms[0].hi, tag);
+    llg_affine(a, ms, fa, fb);
+  }
+
+  // Finish stage g with the raw coupling sum hraw = (W x)_node, then
+  // publish the next stage's m^x under next_tag.
+  __device__ __forceinline__ void stage(const KArgs& a, int node, long long g, float hraw,
+                                        const Publisher& pub, unsigned next_tag) {
+    const int st = static_cast<int>(g & 3);
+    if (a.rec_h) {
+      const size_t n = static_cast<size_t>(g >> 2);
+      a.rec_h[(n * 4 + st) * a.N + node] = hraw;
+      if (st == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) a.rec_m[(n * 3 + i) * a.N + node] = make_float2(mn[i].hi, mn[i].lo);
+      }
+    }
+    const df hx = df_add(df_mul_f(a.acp, hraw), hin);
+    df d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = df_add(fa[i], df_mul(hx, fb[i]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (st == 0) {
+        ksum[i] = d[i];
+        ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
+      } else if (st == 1) {
+        ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
+        ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
+      } else if (st == 2) {
+        ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
+        ms[i] = df_add(mn[i], d[i]);
+      } else {
+        ksum[i] = df_add(ksum[i], d[i]);
+        mn[i] = df_add(mn[i], df_mul(ksum[i], a.sixth));
+        ms[i] = mn[i];
+      }
+    }
+    if (st == 3 && ++sub == a.S) {  // end of input sample t: sample the state
+      sub = 0;
+      if (a.states_out) {
+        const df v = a.comp == 0 ? mn[0] : (a.comp == 1 ? mn[1] : mn[2]);
+        a.states_out[static_cast<size_t>(t) * a.N + node] = v.hi;
+      }
+      if (++t < a.T) load_hin(a, node);
+    }
+    pub(node, ms[0].hi, next_tag);
+    llg_affine(a, ms, fa, fb);  // for the next stage, overlapping the exchange
+  }
+
+  __device__ __forceinline__ void finish(const KArgs& a, int node) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.state[static_cast<size_t>(i) * a.N + node] = df_to_double(mn[i]);
+  }
+};
+
+// Discrete adjoint of the RK4 step, run backwards over a recorded segment.
+// For step m' = m + dt/6 (k1 + 2 k2 + 2 k3 + k4), k_s = f(y_s), and the
+// cotangent lam = dL/dm':
+//   kb4 = dt/6 lam,            yb4 = J(y4)^T kb4
+//   kb3 = dt/3 lam + dt yb4,   yb3 = J(y3)^T kb3
+//   kb2 = dt/3 lam + dt/2 yb3, yb2 = J(y2)^T kb2
+//   kb1 = dt/6 lam + dt/2 yb2, yb1 = J(y1)^T kb1,   lam <- lam + sum yb_s.
+// J^T v splits into a local part and the coupling part A_cp W^T gbar, where
+// gbar_k = bbar_x,k is what the engine exchanges and reduces (with W^T).
+// With b the full field at m (derivation in the design notes):
+//   bbar = gamma' (m x v) - alpha gamma' m x (m x v)            (so gbar is a
+//          fixed linear form of v: cheap once v is known),
+//   mbar = -gamma' [b x v + alpha ((m.b) v + (m.v) b - 2 (b.v) m)]
+//          + H_K' bbar_z e_z + H_s (bbar x p) - (bbar.c) lambda H_s / (1 + lambda m.p) p.
+// Only gbar sits on the critical path; mbar and the parameter terms are
+// formed after publishing, while the exchange is in flight.  Double-float
+// throughout: the A_cp gradient is a strongly cancelling sum over stages.
+struct AdjointProgram {
+  df lam[3], lacc[3], mbar[3];
+  df y[4][3], hx[4];
+  float hraw[4];
+  df gacp, gcur, sumg, hin;
+  long long n;        // current RK4 step (counting down)
+  int si;             // current stage index 0..3 (stage 1..4)
+
+  __device__ __forceinline__ static void cross(const df a[3], const df b[3], df r[3]) {
+    r[0] = df_cross1(a[1], b[2], a[2], b[1]);
+    r[1] = df_cross1(a[2], b[0], a[0], b[2]);
+    r[2] = df_cross1(a[0], b[1], a[1], b[0]);
+  }
+  __device__ __forceinline__ static df dot(const df a[3], const df b[3]) {
+    return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+  }
+
+  __device__ __forceinline__ void setup_step(const KArgs& a, int node) {
+    const int S = a.S;
+    const int t = static_cast<int>(n / S), sb = static_cast<int>(n % S);
+    if (sb == S - 1) {  // the state after this step is sample t; its input field
+      lam[a.comp] = df_add_f(lam[a.comp], a.dLds[static_cast<size_t>(t) * a.N + node]);
+      double s = 0.0;
+      for (int jj = 0; jj < a.n_in; ++jj)
+        s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
+             static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
+      hin = df_from_double(a.ain_g * s);
+    }
+    df m[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float2 v = a.rec_m[(static_cast<size_t>(n) * 3 + i) * a.N + node];
+      m[i] = df{v.x, v.y};
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hraw[q] = a.rec_h[(static_cast<size_t>(n) * 4 + q) * a.N + node];
+      hx[q] = df_add(df_mul_f(a.acp, hraw[q]), hin);
+    }
+    // stage points, with dt dm/dt = A + h B exactly as the forward formed them
+    df A[3], B[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[0][i] = m[i];
+    llg_affine(a, y[0], A, B);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[1][i] = df_add(m[i], df_scale2(df_add(A[i], df_mul(hx[0], B[i])), 0.5f));
+    llg_affine(a, y[1], A, B);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[2][i] = df_add(m[i], df_scale2(df_add(A[i], df_mul(hx[1], B[i])), 0.5f));
+    llg_affine(a, y[2], A, B);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      y[3][i] = df_add(m[i], df_add(A[i], df_mul(hx[2], B[i])));
+      lacc[i] = df{0.f, 0.f};
+    }
+  }
+
+  // gbar = bbar_x at stage point q for cotangent v (in units of 1/dt: the
+  // dt of kbar is applied here, gamma' dt = -gdt)
+  __device__ __forceinline__ df gbar_of(const KArgs& a, int q, const df v[3]) const {
+    const df* m = y[q];
+    // (m x v)_x - alpha (m x (m x v))_x,  m x (m x v) = (m.v) m - |m|^2 v
+    const df mxv_x = df_cross1(m[1], v[2], m[2], v[1]);
+    const df mv = dot(m, v);
+    const df mm = dot(m, m);
+    const df mmv_x = df_sub(df_mul(mv, m[0]), df_mul(mm, v[0]));
+    return df_mul(df_neg(a.gdt), df_sub(mxv_x, df_mul(a.alpha, mmv_x)));
+  }
+
+  // the rest of J(y_q)^T v: mbar (local part) and the parameter terms
+  __device__ __forceinline__ void local_vjp(const KArgs& a, int q, const df v[3], df gb) {
+    const df* m = y[q];
+    const df p[3] = {a.px, a.py, a.pz};
+    const df gpd = df_neg(a.gdt);  // gamma' dt (the dt of v)
+    const df s = dot(m, p);
+    const df rD = df_rcp(df_add_f(df_mul(a.lambda, s), 1.0f));
+    const df hs = df_mul(a.hs0, rD);
+    df c[3], b[3];
+    cross(p, m, c);
+    b[0] = df_add(hx[q], df_mul(hs, c[0]));
+    b[1] = df_mul(hs, c[1]);
+    b[2] = df_add(df_add(a.happl, df_mul(a.hkp, m[2])), df_mul(hs, c[2]));
+    df mv[3], mmv[3], bb[3], bxv[3], bbxp[3];
+    cross(m, v, mv);
+    cross(m, mv, mmv);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) bb[i] = df_mul(gpd, df_sub(mv[i], df_mul(a.alpha, mmv[i])));
+    cross(b, v, bxv);
+    const df mb = dot(m, b), mvd = dot(m, v), bv = dot(b, v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const df inner = df_add(df_add(df_mul(mb, v[i]), df_mul(mvd, b[i])), df_scale2(df_mul(bv, m[i]), -2.0f));
+      mbar[i] = df_neg(df_mul(gpd, df_add(bxv[i], df_mul(a.alpha, inner))));
+    }
+    mbar[2] = df_add(mbar[2], df_mul(a.hkp, bb[2]));
+    cross(bb, p, bbxp);
+    const df bc = dot(bb, c);
+    const df lam_term = df_mul(df_mul(bc, a.lambda), df_mul(hs, rD));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) mbar[i] = df_sub(df_add(mbar[i], df_mul(hs, bbxp[i])), df_mul(lam_term, p[i]));
+    gacp = df_add(gacp, df_mul_f(gb, hraw[q]));
+    gcur = df_add(gcur, df_mul(df_mul_f(bc, a.dhs0_di_f), rD));
+    sumg = df_add(sumg, gb);
+  }
+
+  // kbar / dt for stage index q from lam and yb (the ybar of stage q + 1)
+  __device__ __forceinline__ void kbar(int q, const df yb[3], df v[3]) const {
+    // dt/6, dt/3, dt/3, dt/6 on lam; 0, dt, dt/2, dt/2 on yb; the common dt
+    // is folded into gamma' dt in gbar_of / local_vjp
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const df l = (q == 3 || q == 0) ? df_mul(lam[i], df{0.16666667f, -4.967054e-09f})
+                                      : df_mul(lam[i], df{0.33333334f, -9.934108e-09f});
+      v[i] = q == 3 ? l : df_add(l, q == 2 ? yb[i] : df_scale2(yb[i], 0.5f));
+    }
+  }
+
+  __device__ __forceinline__ void publish_stage(const KArgs& a, int node, int q, const df v[3],
+                                                const Publisher& pub, unsigned tag) {
+    const df gb = gbar_of(a, q, v);
+    pub(node, gb.hi, tag);
+    local_vjp(a, q, v, gb);  // overlaps the exchange
+  }
+
+  __device__ __forceinline__ void init(const KArgs& a, int node, const Publisher& pub, unsigned tag) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = df_from_double(a.lam[static_cast<size_t>(i) * a.N + node]);
+    gacp = gcur = sumg = hin = df{0.f, 0.f};
+    n = static_cast<long long>(a.T) * a.S - 1;
+    setup_step(a, node);
+    si = 3;
+    const df zero[3] = {df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}};
+    df v[3];
+    kbar(3, zero, v);
+    publish_stage(a, node, 3, v, pub, tag);
+  }
+
+  // q = (W^T gbar)_node for the current stage
+  __device__ __forceinline__ void stage(const KArgs& a, int node, long long /*g*/, float q,
+                                        const Publisher& pub, unsigned next_tag) {
+    // ybar of this stage; the coupling part carries the dt folded into gbar
+    df yb[3] = {df_add(mbar[0], df_mul_f(a.acp, q)), mbar[1], mbar[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lacc[i] = df_add(lacc[i], yb[i]);
+    if (si > 0) {
+      --si;
+      df v[3];
+      kbar(si, yb, v);
+      publish_stage(a, node, si, v, pub, next_tag);
+      return;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = df_add(lam[i], lacc[i]);
+    if (n % a.S == 0) {  // first RK4 step of its sample: flush dL/dw_in
+      const int t = static_cast<int>(n / a.S);
+      const double sg = df_to_double(sumg);
+      for (int jj = 0; jj < a.n_in; ++jj)
+        a.g_win[static_cast<size_t>(node) * a.n_in + jj] +=
+            a.ain_g * static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]) * sg;
+      sumg = df{0.f, 0.f};
+    }
+    if (--n >= 0) {
+      setup_step(a, node);
+      si = 3;
+      const df zero[3] = {df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}};
+      df v[3];
+      kbar(3, zero, v);
+      publish_stage(a, node, 3, v, pub, next_tag);
+    }
+  }
+
+  __device__ __forceinline__ void finish(const KArgs& a, int node) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.lam[static_cast<size_t>(i) * a.N + node] = df_to_double(lam[i]);
+    a.g_acp[node] += df_to_double(gacp);
+    a.g_cur[node] += df_to_double(gcur);
+  }
+};
+
 // ------------------------------------------------------------ the stepper
 
 // kRowMajorW = false: a.W is the tiled copy made by sto_create (one bulk copy
 // per panel).  kRowMajorW = true: a.W is the caller's row-major N x N matrix
 // (N a multiple of 4); each panel arrives as one bulk copy per row, issued by
 // the 32 lanes of the producer warp.  Consumers are identical in both.
-template <int RPW, bool kRowMajorW>
+template <int RPW, bool kRowMajorW, bool kAdjoint = false>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int c = blockIdx.x;
@@ -409,26 +718,14 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   const int ctid = tid;
   const int node = r0 + ctid;
   const bool owner = ctid < R;
-  const bool publish = (G > 1) && (c != a.inject_cta);
-  // state of the owned oscillator in double-float: m_n, stage state, RK4 sum,
-  // and the affine parts A, B of the next increment
-  df mn[3], ms[3], ksum[3], fa[3], fb[3], hin = {0.f, 0.f};
-  // owners sit in the first warps; the others gather while owners form A, B
+  const Publisher pub{a.xbuf, xs, a.N, G == 1, c != a.inject_cta};
+  // owners sit in the first warps; the others gather while owners work
   const int owner_warps = (R_max + 31) / 32;
   const int gather_first = owner_warps < kConsWarps ? owner_warps * 32 : 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    mn[i] = owner ? df_from_double(a.state[static_cast<size_t>(i) * a.N + node]) : df{0.f, 0.f};
-    ms[i] = mn[i];
-    ksum[i] = df{0.f, 0.f};
-  }
+  using Program = typename std::conditional<kAdjoint, AdjointProgram, ForwardProgram>::type;
+  Program prog;
   unsigned tag = a.tag_base;
-  if (owner) {
-    if (G == 1) xs[node] = ms[0].hi;
-    else if (publish)
-      st_relaxed_u64(a.xbuf + static_cast<size_t>(tag & 1u) * a.N + node, pack_x(ms[0].hi, tag));
-    llg_affine(a, ms, fa, fb);
-  }
+  if (owner) prog.init(a, node, pub, tag);
 
   int cslot = 0;
   uint32_t cphase = 0;
@@ -445,167 +742,122 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
     }
     aborted = consumer_sync_or(!landed);
   }
-  for (int t = 0; t < a.T && !aborted; ++t) {
-    if (owner) {
-      double s = 0.0;
-      for (int jj = 0; jj < a.n_in; ++jj)
-        s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
-             static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
-      hin = df_from_double(a.ain_g * s);
+  const long long n_stages = 4LL * a.S * a.T;
+  for (long long g = 0; g < n_stages && !aborted; ++g) {
+    // 1. the stage's published value of every oscillator
+    bool fail = false;
+    if (G > 1 && ctid >= gather_first &&
+        !gather_x(a, xs, tag, ctid - gather_first, kCons - gather_first)) {
+      fail = true;
+      *s_abort = 1;
     }
-    for (int sub = 0; sub < a.S && !aborted; ++sub) {
-      for (int st = 0; st < 4; ++st) {
-        // 1. the stage's m^x of every oscillator
-        bool fail = false;
-        if (G > 1 && ctid >= gather_first &&
-            !gather_x(a, xs, tag, ctid - gather_first, kCons - gather_first)) {
-          fail = true;
-          *s_abort = 1;
-        }
-        if (consumer_sync_or(fail)) { aborted = true; break; }
-
-        // 2. h = W x over this CTA's rows, panel by panel
-        float acc[RPW];
+    if (consumer_sync_or(fail)) { aborted = true; break; }
+    // 2. h = W x over this CTA's rows, panel by panel
+    float acc[RPW];
 #pragma unroll
-        for (int qq = 0; qq < RPW; ++qq) acc[qq] = 0.f;
-        const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
-        if (a.resident) {
-          // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
-          // with few rows per warp, four partial sums per row shorten the
-          // dependent FMA chain
-          constexpr int kPart = RPW <= 2 ? 4 : 1;
-          float part[RPW][kPart];
+    for (int qq = 0; qq < RPW; ++qq) acc[qq] = 0.f;
+    const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
+    if (a.resident) {
+      // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
+      // with few rows per warp, four partial sums per row shorten the
+      // dependent FMA chain
+      constexpr int kPart = RPW <= 2 ? 4 : 1;
+      float part[RPW][kPart];
 #pragma unroll
-          for (int qq = 0; qq < RPW; ++qq)
+      for (int qq = 0; qq < RPW; ++qq)
 #pragma unroll
-            for (int k = 0; k < kPart; ++k) part[qq][k] = 0.f;
-          const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
-          const int pstride = static_cast<int>(slot_floats / 4);
+        for (int k = 0; k < kPart; ++k) part[qq][k] = 0.f;
+      const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
+      const int pstride = static_cast<int>(slot_floats / 4);
 #pragma unroll 4
-          for (int j = 0; j < a.P; ++j) {
-            const float4 xv = x4[j * (kPanelCols / 4)];
-            const float4* pj = w4 + j * pstride;
+      for (int j = 0; j < a.P; ++j) {
+        const float4 xv = x4[j * (kPanelCols / 4)];
+        const float4* pj = w4 + j * pstride;
 #pragma unroll
-            for (int qq = 0; qq < RPW; ++qq) {
-              const int r = warp + qq * kConsWarps;
-              if (r < R) {
-                const float4 w = pj[r * (kPanelCols / 4)];
-                if constexpr (kPart == 4) {
-                  part[qq][0] = fmaf(w.x, xv.x, part[qq][0]);
-                  part[qq][1] = fmaf(w.y, xv.y, part[qq][1]);
-                  part[qq][2] = fmaf(w.z, xv.z, part[qq][2]);
-                  part[qq][3] = fmaf(w.w, xv.w, part[qq][3]);
-                } else {
-                  float v = part[qq][0];
-                  v = fmaf(w.x, xv.x, v);
-                  v = fmaf(w.y, xv.y, v);
-                  v = fmaf(w.z, xv.z, v);
-                  v = fmaf(w.w, xv.w, v);
-                  part[qq][0] = v;
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int qq = 0; qq < RPW; ++qq) {
-            if constexpr (kPart == 4)
-              acc[qq] = (part[qq][0] + part[qq][1]) + (part[qq][2] + part[qq][3]);
-            else
-              acc[qq] = part[qq][0];
-          }
-        } else {
-          for (int j = 0; j < a.P; ++j) {
-            const int slot = cslot;
-            // every lane waits; the vote keeps the warp's decision uniform
-            const bool landed = mbar_wait_bounded(&full[slot], cphase, a.timeout_ns, s_abort);
-            if (!__all_sync(0xffffffffu, landed)) {
-              if (lane == 0) {
-                if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
-                *s_abort = 1;
-              }
-              fail = true;
-              break;
-            }
-            const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
-            const float4 xv = x4[j * (kPanelCols / 4)];
-#pragma unroll
-            for (int qq = 0; qq < RPW; ++qq) {
-              const int r = warp + qq * kConsWarps;
-              if (r < R) {
-                const float4 w = p4[r * (kPanelCols / 4) + lane];
-                float v = acc[qq];
-                v = fmaf(w.x, xv.x, v);
-                v = fmaf(w.y, xv.y, v);
-                v = fmaf(w.z, xv.z, v);
-                v = fmaf(w.w, xv.w, v);
-                acc[qq] = v;
-              }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            if (++cslot == a.ns) {
-              cslot = 0;
-              cphase ^= 1u;
-            }
-          }
-        }
-        // butterfly sums of all rows at once (rows past R hold 0), so the
-        // shuffle chains of different rows overlap
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-          for (int qq = 0; qq < RPW; ++qq) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], off);
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int qq = 0; qq < RPW; ++qq) {
-            const int r = warp + qq * kConsWarps;
-            if (r < R) hs[r] = acc[qq];
-          }
-        }
-        if (consumer_sync_or(fail)) { aborted = true; break; }
-
-        // 3. torque, RK4 stage combination, publish the next stage's m^x
-        if (owner) {
-          const df hx = df_add(df_mul_f(a.acp, hs[ctid]), hin);
-          df d[3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) d[i] = df_add(fa[i], df_mul(hx, fb[i]));
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            if (st == 0) {
-              ksum[i] = d[i];
-              ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
-            } else if (st == 1) {
-              ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
-              ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
-            } else if (st == 2) {
-              ksum[i] = df_add(ksum[i], df_scale2(d[i], 2.0f));
-              ms[i] = df_add(mn[i], d[i]);
+        for (int qq = 0; qq < RPW; ++qq) {
+          const int r = warp + qq * kConsWarps;
+          if (r < R) {
+            const float4 w = pj[r * (kPanelCols / 4)];
+            if constexpr (kPart == 4) {
+              part[qq][0] = fmaf(w.x, xv.x, part[qq][0]);
+              part[qq][1] = fmaf(w.y, xv.y, part[qq][1]);
+              part[qq][2] = fmaf(w.z, xv.z, part[qq][2]);
+              part[qq][3] = fmaf(w.w, xv.w, part[qq][3]);
             } else {
-              ksum[i] = df_add(ksum[i], d[i]);
-              mn[i] = df_add(mn[i], df_mul(ksum[i], a.sixth));
-              ms[i] = mn[i];
+              float v = part[qq][0];
+              v = fmaf(w.x, xv.x, v);
+              v = fmaf(w.y, xv.y, v);
+              v = fmaf(w.z, xv.z, v);
+              v = fmaf(w.w, xv.w, v);
+              part[qq][0] = v;
             }
           }
-          const unsigned nt = tag + 1u;
-          if (G == 1) xs[node] = ms[0].hi;
-          else if (publish)
-            st_relaxed_u64(a.xbuf + static_cast<size_t>(nt & 1u) * a.N + node, pack_x(ms[0].hi, nt));
-          llg_affine(a, ms, fa, fb);  // for the next stage, overlapping the exchange
         }
-        ++tag;
+      }
+#pragma unroll
+      for (int qq = 0; qq < RPW; ++qq) {
+        if constexpr (kPart == 4)
+          acc[qq] = (part[qq][0] + part[qq][1]) + (part[qq][2] + part[qq][3]);
+        else
+          acc[qq] = part[qq][0];
+      }
+    } else {
+      for (int j = 0; j < a.P; ++j) {
+        const int slot = cslot;
+        // every lane waits; the vote keeps the warp's decision uniform
+        const bool landed = mbar_wait_bounded(&full[slot], cphase, a.timeout_ns, s_abort);
+        if (!__all_sync(0xffffffffu, landed)) {
+          if (lane == 0) {
+            if (!*s_abort) report_error(a.err, kErrTimeout, c, tag, kSiteFull);
+            *s_abort = 1;
+          }
+          fail = true;
+          break;
+        }
+        const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
+        const float4 xv = x4[j * (kPanelCols / 4)];
+#pragma unroll
+        for (int qq = 0; qq < RPW; ++qq) {
+          const int r = warp + qq * kConsWarps;
+          if (r < R) {
+            const float4 w = p4[r * (kPanelCols / 4) + lane];
+            float v = acc[qq];
+            v = fmaf(w.x, xv.x, v);
+            v = fmaf(w.y, xv.y, v);
+            v = fmaf(w.z, xv.z, v);
+            v = fmaf(w.w, xv.w, v);
+            acc[qq] = v;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (++cslot == a.ns) {
+          cslot = 0;
+          cphase ^= 1u;
+        }
       }
     }
-    if (!aborted && owner && a.states_out) {
-      const df v = a.comp == 0 ? mn[0] : (a.comp == 1 ? mn[1] : mn[2]);
-      a.states_out[static_cast<size_t>(t) * a.N + node] = v.hi;
-    }
-  }
-  if (!aborted && owner) {
+    // butterfly sums of all rows at once (rows past R hold 0), so the
+    // shuffle chains of different rows overlap
 #pragma unroll
-    for (int i = 0; i < 3; ++i) a.state[static_cast<size_t>(i) * a.N + node] = df_to_double(mn[i]);
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int qq = 0; qq < RPW; ++qq) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int qq = 0; qq < RPW; ++qq) {
+        const int r = warp + qq * kConsWarps;
+        if (r < R) hs[r] = acc[qq];
+      }
+    }
+    if (consumer_sync_or(fail)) { aborted = true; break; }
+
+    // 3. the owner's program finishes the stage and publishes the next
+    if (owner) prog.stage(a, node, g, hs[ctid], pub, tag + 1u);
+    ++tag;
   }
+  if (!aborted && owner) prog.finish(a, node);
 }
 
 // Scatter a row-major N x N matrix into the tiled layout: CTA c's rows
@@ -632,6 +884,38 @@ __global__ void tile_w_kernel(const float* __restrict__ W, float* __restrict__ W
     const int r = k - r0, j = i / kPanelCols, col = i % kPanelCols;
     Wt[static_cast<size_t>(r0) * P * kPanelCols + static_cast<size_t>(j) * R * kPanelCols +
        static_cast<size_t>(r) * kPanelCols + col] = W[idx];
+  }
+}
+
+// Row block and offset of row k in the tiled layout of a plan with G CTAs.
+__device__ __forceinline__ void tiled_row(int N, int G, int k, int* r0, int* R) {
+  const int q = N / G, rem = N % G;
+  if (k < rem * (q + 1)) {
+    *r0 = (k / (q + 1)) * (q + 1);
+    *R = q + 1;
+  } else {
+    *r0 = ((k - rem * (q + 1)) / q) * q + rem * (q + 1);
+    *R = q;
+  }
+}
+
+// W^T in the tiled layout, read from W in the same layout.  The destination
+// must be zeroed beforehand (its padding columns stay zero).
+__global__ void transpose_tiled_kernel(const float* __restrict__ Wt, float* __restrict__ WTt, int N,
+                                       int G, int P) {
+  const long long total = static_cast<long long>(N) * N;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(idx / N), i = static_cast<int>(idx % N);  // W[k][i]
+    int r0, R;
+    tiled_row(N, G, k, &r0, &R);
+    const float v = Wt[static_cast<size_t>(r0) * P * kPanelCols +
+                       static_cast<size_t>(i / kPanelCols) * R * kPanelCols +
+                       static_cast<size_t>(k - r0) * kPanelCols + i % kPanelCols];
+    int s0, S0;
+    tiled_row(N, G, i, &s0, &S0);  // W^T[i][k]
+    WTt[static_cast<size_t>(s0) * P * kPanelCols + static_cast<size_t>(k / kPanelCols) * S0 * kPanelCols +
+        static_cast<size_t>(i - s0) * kPanelCols + k % kPanelCols] = v;
   }
 }
 

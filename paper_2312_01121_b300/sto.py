@@ -58,6 +58,11 @@ class sto_info(ctypes.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class sto_grads(ctypes.Structure):
+    _fields_ = [("dA_cp", ctypes.c_double), ("dcurrent", ctypes.c_double),
+                ("dw_in", ctypes.c_void_p), ("dm0", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); the exported symbols of include/sto.h
 _VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
 SIGNATURES = {
@@ -79,6 +84,8 @@ SIGNATURES = {
     "sto_debug_inject_stall": (ctypes.c_int, [_VP, _I32]),
     "sto_run_noalloc": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
                                        _I64, _VP, _VP]),
+    "sto_adjoint": (ctypes.c_int, [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sto_grads)]),
+    "sto_set_input_weights": (ctypes.c_int, [_VP, _VP]),
 }
 
 _lib = None
@@ -229,6 +236,28 @@ def sto_get_state_f64(h, out):
     _check(load_library().sto_get_state_f64(h, p))
 
 
+def sto_adjoint(h, u, T, dL_dstates, ckpt_every=100, dw_in=None, dm0=None) -> dict:
+    """Gradients of sum(dL_dstates * states) of the run from the current state
+    (see include/sto.h).  dw_in (N x n_in) and dm0 (3 x N) are optional float64
+    outputs (numpy or torch).  Returns {"A_cp", "current"} (and fills the rest)."""
+    pu, ku = _ptr(u, np.float32)
+    pg, kg = _ptr(dL_dstates, np.float32)
+    pw, kw = _ptr(dw_in, np.float64) if dw_in is not None else (None, None)
+    pm, km = _ptr(dm0, np.float64) if dm0 is not None else (None, None)
+    if dw_in is not None and not hasattr(dw_in, "data_ptr") and kw is not dw_in:
+        raise TypeError("dw_in must be a contiguous float64 array")
+    if dm0 is not None and not hasattr(dm0, "data_ptr") and km is not dm0:
+        raise TypeError("dm0 must be a contiguous float64 array")
+    g = sto_grads(0.0, 0.0, pw, pm)
+    _check(load_library().sto_adjoint(h, pu, T, pg, int(ckpt_every), ctypes.byref(g)))
+    return {"A_cp": g.dA_cp, "current": g.dcurrent}
+
+
+def sto_set_input_weights(h, w_in):
+    p, k = _ptr(w_in, np.float32)
+    _check(load_library().sto_set_input_weights(h, p))
+
+
 def sto_get_info(h) -> dict:
     info = sto_info()
     _check(load_library().sto_get_info(h, ctypes.byref(info)))
@@ -278,6 +307,24 @@ class Reservoir:
             T = int(u.shape[0])
         sto_run(self.handle, u, T, states_out)
         return states_out
+
+    def adjoint(self, u, dL_dstates, ckpt_every=100, T=None, want_w_in=True, want_m0=True):
+        """Gradients of sum(dL_dstates * states) for the run from the current
+        state; the state advances as in run().  Returns a dict with A_cp,
+        current, and (numpy float64) w_in (N x n_in) and m0 (3 x N)."""
+        if T is None:
+            T = int(u.shape[0])
+        dw = np.zeros((self.N, self.params.n_in)) if want_w_in else None
+        dm = np.zeros((3, self.N)) if want_m0 else None
+        g = sto_adjoint(self.handle, u, T, dL_dstates, ckpt_every, dw, dm)
+        if want_w_in:
+            g["w_in"] = dw
+        if want_m0:
+            g["m0"] = dm
+        return g
+
+    def set_input_weights(self, w_in):
+        sto_set_input_weights(self.handle, w_in)
 
     def set_params(self, params: Params):
         sto_set_params(self.handle, params)
