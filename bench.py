@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-n", type=int, default=1000)
+    ap.add_argument("--adj-t", type=int, default=40, help="input samples per adjoint call")
+    ap.add_argument("--adj-k", type=int, default=20, help="checkpoint interval (samples)")
     return ap.parse_args()
 
 
@@ -62,6 +66,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank simulates its own independent reservoir (weak scaling)."""
+    return rank
+
+
+def combine_ranks(total_ms, e2e_s, updates, world, all_reduce_max=None):
+    """Whole-job throughput over `world` replicas: the slowest rank's time
+    (max over ranks of the timed region) and the sum of node-updates."""
+    if world > 1:
+        total_ms, e2e_s = all_reduce_max([total_ms, e2e_s or 0.0])
+        updates *= world
+    value = updates / (total_ms / 1e3)
+    e2e_value = updates / e2e_s if e2e_s else None
+    return value, e2e_value, total_ms, updates
 
 
 def workload(N, T, seed):
@@ -212,6 +232,36 @@ def time_device(N, args, ips, seed, torch, sto, dev):
     return out
 
 
+def time_adjoint(args, seed, torch, sto, dev):
+    """sto_adjoint on the N = 10^3 reservoir (readout-loss gradients): node-updates of
+    the differentiated run per second of the whole adjoint call (checkpoint pass,
+    recomputation with recording, reverse pass)."""
+    N, T, K = args.adj_n, args.adj_t, args.adj_k
+    W, w_in, m0, u = workload(N, T, seed)
+    P = sto.Params(substeps=args.substeps)
+    stream = torch.cuda.current_stream()
+    res = sto.Reservoir(torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), P,
+                        m0=torch.from_numpy(m0).to(dev), stream=stream)
+    u_d = torch.from_numpy(u).to(dev)
+    g = torch.from_numpy(np.random.default_rng(seed).standard_normal((T, N)).astype(np.float32)).to(dev)
+    res.adjoint(u_d, g, K)  # warm-up (builds W^T, allocates the recording)
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        res.set_state(m0)
+        res.adjoint(u_d, g, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res.close()
+    return {"N": N, "input_samples": T, "ckpt_every": K, "ms_per_call": ms,
+            "value": N * T * args.substeps / (ms / 1e3), "unit": "node-updates/s",
+            "note": "gradients of a loss on the sampled states w.r.t. A_cp, I, w_in, m0; "
+                    "one call = checkpoint pass + recomputation with recording + reverse pass"}
+
+
 def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
     """Node-updates/s of the FP64 oracle on a bounded sample of the workload."""
     import oracle
@@ -285,20 +335,22 @@ def main():
     build.build()
     sto.load_library()
 
-    main_r = time_device(args.n, args, args.ips, rank, torch, sto, dev)
+    main_r = time_device(args.n, args, args.ips, replica_seed(rank), torch, sto, dev)
     small = None
     if not args.no_small:
-        small = time_device(args.n_small, args, args.ips_small, rank, torch, sto, dev)
+        small = time_device(args.n_small, args, args.ips_small, replica_seed(rank), torch, sto, dev)
 
-    tot_ms = main_r["total_ms"]
-    updates = main_r["node_updates"]
-    e2e_s = main_r.get("e2e_s")
-    if world > 1:
-        t = torch.tensor([tot_ms, e2e_s or 0.0], device=dev, dtype=torch.float64)
+    def reduce_max(vals):
+        t = torch.tensor(vals, device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms, e2e_s = float(t[0]), float(t[1])
-        updates *= world
-    value = updates / (tot_ms / 1e3)
+        return [float(x) for x in t]
+
+    adj = None
+    if not args.no_adjoint:
+        adj = time_adjoint(args, replica_seed(rank), torch, sto, dev)
+
+    value, e2e_value, tot_ms, updates = combine_ranks(
+        main_r["total_ms"], main_r.get("e2e_s"), main_r["node_updates"], world, reduce_max)
 
     # roofline of the stepper: algorithmic bytes per launch / mean launch time
     N, ips, S = args.n, args.ips, args.substeps
@@ -352,8 +404,8 @@ def main():
         "gpu_launches": args.steps,
         "check": {"finite": main_r["finite"], "max_abs_norm_minus_1": main_r["norm_err"]},
     }
-    if e2e_s:
-        line["e2e"] = {"value": updates / e2e_s, "unit": "node-updates/s",
+    if e2e_value:
+        line["e2e"] = {"value": e2e_value, "unit": "node-updates/s",
                        "h2d_bytes_per_step": main_r["h2d_bytes_per_step"],
                        "d2h_bytes_per_step": main_r["d2h_bytes_per_step"]}
     if cpu is not None:
@@ -378,6 +430,8 @@ def main():
             "plan": small["info"], "clocks": small["clocks"],
             "e2e_value": (small["node_updates"] / small["e2e_s"]) if small.get("e2e_s") else None,
         }
+    if adj is not None:
+        line["adjoint"] = adj
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

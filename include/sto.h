@@ -214,6 +214,46 @@ STO_API int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* d
  * Errors: STO_EINVAL, STO_ENONFINITE, STO_ECUDA. */
 STO_API int sto_set_input_weights(sto_handle* h, const float* w_in);
 
+/* ------------------------------------------------------------------------
+ * Batched parameter sweep (Sec. 1 and Sec. 2: exploring the parameter space
+ * is the time-consuming part).  R reservoirs share one coupling matrix W and
+ * the input weights, and differ in their current I_r and input gain g_r; all
+ * are driven by the same input series.  Per RK4 stage the coupling of all
+ * reservoirs is one dense product W [m^x_0 ... m^x_{R-1}] on the tensor cores
+ * (tcgen05, BF16 W, the stage values split into two BF16 terms, FP32
+ * accumulation), followed by the double-float torque and RK4 combination of
+ * every (reservoir, oscillator) pair.  W is rounded to BF16 once, at
+ * creation: results match the single-reservoir method run with that W.
+ * ------------------------------------------------------------------------ */
+typedef struct sto_batch sto_batch; /* opaque */
+
+/* Create a sweep of R reservoirs of N oscillators.
+ *   params      shared parameters (substeps, dt, A_cp, n_in, ...).
+ *   current     R currents I_r in A, or NULL for params->current.
+ *   input_gain  R gains g_r, or NULL for params->input_gain.
+ *   W           N x N float32 (host or device), rounded to BF16.
+ *   w_in        N x n_in float32 (host or device), shared.
+ *   m0          R x 3 x N float32 initial states (reservoir-major; host or
+ *               device) or NULL for Eq. (initial).
+ * Errors: STO_EINVAL, STO_ENONFINITE, STO_ENOMEM, STO_ENOTSUP, STO_ECUDA. */
+STO_API int sto_batch_create(int64_t N, int32_t R, const sto_params* params,
+                             const double* current, const double* input_gain,
+                             const float* W, const float* w_in, const float* m0,
+                             void* stream, sto_batch** out);
+
+/* Advance every reservoir over T input samples of the shared series u
+ * (T x n_in, host or device).  states_out: T x R x N float32 (sample,
+ * reservoir, oscillator; host or device) or NULL.  One input sample is
+ * captured as a CUDA graph (substeps x 4 pairs of product and torque
+ * kernels) and replayed T times.
+ * Errors: STO_EINVAL, STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA. */
+STO_API int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out);
+
+/* FP64 states, R x 3 x N (host or device). */
+STO_API int sto_batch_get_state(const sto_batch* b, double* m);
+
+STO_API void sto_batch_destroy(sto_batch* b);
+
 /* Report the launch plan. */
 STO_API int sto_get_info(const sto_handle* h, sto_info* out);
 

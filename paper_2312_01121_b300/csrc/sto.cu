@@ -17,6 +17,7 @@
 
 #include "sto.h"
 #include "sto_kernel.cuh"
+#include "sweep.cuh"
 
 namespace {
 
@@ -894,6 +895,313 @@ int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const f
   STO_CUDA(cudaStreamSynchronize(s));
   if (h_err[0] != 0) return h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
   return STO_OK;
+}
+
+// ---------------------------------------------------------------- sweep
+
+}  // extern "C"
+
+struct sto_batch {
+  cudaStream_t stream = nullptr;      // the caller's stream
+  cudaStream_t own = nullptr;         // capturable stream the sweep runs on
+  cudaEvent_t ev = nullptr;
+  int64_t N = 0;
+  int32_t R = 0;
+  int Mpad = 0, Kpad = 0, Rpad = 0;
+  sto_params params{};
+  __nv_bfloat16* Wb = nullptr;
+  __nv_bfloat16* Xs = nullptr;
+  float* Dt = nullptr;
+  float* win = nullptr;
+  float2* st = nullptr;       // mn | ms | ksum, each [3][R][N]
+  sto::df* hs0 = nullptr;     // [R]
+  double* aing = nullptr;     // [R]
+  int* t_dev = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  float* d_u = nullptr;
+  size_t d_u_cap = 0;
+  float* d_states = nullptr;
+  size_t d_states_cap = 0;
+};
+
+namespace {
+
+void free_batch(sto_batch* b) {
+  if (!b) return;
+  cudaFree(b->Wb);
+  cudaFree(b->Xs);
+  cudaFree(b->Dt);
+  cudaFree(b->win);
+  cudaFree(b->st);
+  cudaFree(b->hs0);
+  cudaFree(b->aing);
+  cudaFree(b->t_dev);
+  cudaFree(b->d_err);
+  cudaFree(b->d_u);
+  cudaFree(b->d_states);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+}
+
+// Enqueue one input sample of the sweep: S RK4 steps of four
+// (tensor-core product, epilogue) pairs, then advance the sample counter.
+int batch_enqueue_sample(sto_batch* b, const float* d_u, float* d_states) {
+  const sto_params& P = b->params;
+  cudaStream_t s = b->own;
+  sto::GemmArgs g{};
+  g.Wb = b->Wb;
+  g.Xs = b->Xs;
+  g.Dt = b->Dt;
+  g.err = b->d_err;
+  g.N = static_cast<int>(b->N);
+  g.R = b->R;
+  g.Kpad = b->Kpad;
+  g.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
+  sto::EpiArgs e{};
+  e.Dt = b->Dt;
+  e.w_in = b->win;
+  e.u = d_u;
+  e.t_dev = b->t_dev;
+  const size_t RN = static_cast<size_t>(b->R) * b->N;
+  e.mn = b->st;
+  e.ms = b->st + 3 * RN;
+  e.ksum = b->st + 6 * RN;
+  e.Xs = b->Xs;
+  e.states_out = d_states;
+  e.hs0_r = b->hs0;
+  e.ain_g_r = b->aing;
+  e.N = static_cast<int>(b->N);
+  e.R = b->R;
+  e.Kpad = b->Kpad;
+  e.n_in = P.n_in;
+  e.comp = P.sample_component;
+  set_constants(P, &e.c);
+  const dim3 ggrid(b->Mpad / sto::kSwM, b->Rpad / sto::kSwN);
+  const unsigned eblocks = static_cast<unsigned>((RN + 255) / 256);
+  for (int sub = 0; sub < P.substeps; ++sub) {
+    for (int st = 0; st < 4; ++st) {
+      sto::sweep_gemm_kernel<<<ggrid, sto::kSwThreads, sto::kSwSmem, s>>>(g);
+      STO_CUDA(cudaGetLastError());
+      e.st = st;
+      e.last_sub = sub == P.substeps - 1;
+      sto::sweep_epilogue_kernel<<<eblocks, 256, 0, s>>>(e);
+      STO_CUDA(cudaGetLastError());
+    }
+  }
+  sto::sweep_advance_kernel<<<1, 1, 0, s>>>(b->t_dev);
+  STO_CUDA(cudaGetLastError());
+  return STO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const double* current,
+                     const double* input_gain, const float* W, const float* w_in,
+                     const float* m0, void* stream, sto_batch** out) {
+  if (!out) return STO_EINVAL;
+  *out = nullptr;
+  if (N < 1 || R < 1 || !W || !w_in) return STO_EINVAL;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (N > 32768 || R > 65536) return STO_ENOTSUP;
+  sto_batch* b = new (std::nothrow) sto_batch();
+  if (!b) return STO_ENOMEM;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->N = N;
+  b->R = R;
+  b->params = *params;
+  b->Mpad = static_cast<int>((N + sto::kSwM - 1) / sto::kSwM * sto::kSwM);
+  b->Kpad = static_cast<int>((N + sto::kSwK - 1) / sto::kSwK * sto::kSwK);
+  b->Rpad = (R + sto::kSwN - 1) / sto::kSwN * sto::kSwN;
+  cudaStream_t s = b->stream;
+  auto fail = [&](int code) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return code;
+  };
+  const size_t RN = static_cast<size_t>(R) * N;
+  const int n_in = params->n_in;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  if (!alloc(reinterpret_cast<void**>(&b->Wb), static_cast<size_t>(b->Mpad) * b->Kpad * 2) ||
+      !alloc(reinterpret_cast<void**>(&b->Xs), static_cast<size_t>(b->Rpad) * 2 * b->Kpad * 2) ||
+      !alloc(reinterpret_cast<void**>(&b->Dt), RN * 4) ||
+      !alloc(reinterpret_cast<void**>(&b->win), static_cast<size_t>(N) * n_in * 4) ||
+      !alloc(reinterpret_cast<void**>(&b->st), 9 * RN * sizeof(float2)) ||
+      !alloc(reinterpret_cast<void**>(&b->hs0), R * sizeof(sto::df)) ||
+      !alloc(reinterpret_cast<void**>(&b->aing), R * sizeof(double)) ||
+      !alloc(reinterpret_cast<void**>(&b->t_dev), 16) ||
+      !alloc(reinterpret_cast<void**>(&b->d_err), 16))
+    return fail(STO_ENOMEM);
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_err), 16) != cudaSuccess) {
+    cudaGetLastError();
+    b->h_err = nullptr;
+    return fail(STO_ENOMEM);
+  }
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  // W -> BF16, zero padded
+  const float* d_src = W;
+  float* d_tmp = nullptr;
+  if (!is_device_ptr(W)) {
+    if (!alloc(reinterpret_cast<void**>(&d_tmp), static_cast<size_t>(N) * N * 4)) return fail(STO_ENOMEM);
+    e = cudaMemcpyAsync(d_tmp, W, static_cast<size_t>(N) * N * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFree(d_tmp); return fail(cuda_fail(e)); }
+    d_src = d_tmp;
+  }
+  bool bad = false;
+  rc = any_nonfinite(d_src, N * N, s, b->d_err, b->h_err, &bad);
+  if (!rc && bad) rc = STO_ENONFINITE;
+  if (!rc) {
+    e = cudaMemsetAsync(b->Wb, 0, static_cast<size_t>(b->Mpad) * b->Kpad * 2, s);
+    if (e == cudaSuccess) {
+      sto::sweep_pack_w_kernel<<<2048, 256, 0, s>>>(d_src, b->Wb, static_cast<int>(N), b->Kpad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (d_tmp) cudaFree(d_tmp);
+  if (rc) return fail(rc);
+  rc = upload_floats(b->win, w_in, static_cast<size_t>(N) * n_in, s);
+  if (!rc) {
+    rc = any_nonfinite(b->win, N * n_in, s, b->d_err, b->h_err, &bad);
+    if (!rc && bad) rc = STO_ENONFINITE;
+  }
+  if (rc) return fail(rc);
+  // per-reservoir constants
+  std::vector<sto::df> hs0(R);
+  std::vector<double> aing(R);
+  const double hs0_per_amp = params->hbar * params->eta * 1.0e7 /
+                             (2.0 * params->e_charge * params->Ms * params->volume);
+  for (int r = 0; r < R; ++r) {
+    const double I = current ? current[r] : params->current;
+    const double gn = input_gain ? input_gain[r] : params->input_gain;
+    if (!std::isfinite(I) || !std::isfinite(gn)) return fail(STO_EINVAL);
+    hs0[r] = sto::df_split_host(hs0_per_amp * I);
+    aing[r] = params->A_in * gn;
+  }
+  if ((e = cudaMemcpyAsync(b->hs0, hs0.data(), R * sizeof(sto::df), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->aing, aing.data(), R * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  // states: mn = ms = m0, ksum = 0  (device layout [3][R][N] df)
+  std::vector<float2> st(9 * RN, make_float2(0.f, 0.f));
+  std::vector<float> mf;
+  if (m0) {
+    rc = fetch_floats(&mf, m0, 3 * RN, s);
+    if (rc) return fail(rc);
+  }
+  const double phi0 = 2.0 * M_PI / 360.0;
+  const double ic[3] = {std::sin(phi0) * std::cos(phi0), std::sin(phi0) * std::sin(phi0), std::cos(phi0)};
+  for (int r = 0; r < R; ++r)
+    for (int i = 0; i < 3; ++i)
+      for (int64_t k = 0; k < N; ++k) {
+        const double v = m0 ? mf[(static_cast<size_t>(r) * 3 + i) * N + k] : ic[i];
+        if (!std::isfinite(v)) return fail(STO_ENONFINITE);
+        const sto::df d = sto::df_split_host(v);
+        st[i * RN + static_cast<size_t>(r) * N + k] = make_float2(d.hi, d.lo);
+        st[3 * RN + i * RN + static_cast<size_t>(r) * N + k] = make_float2(d.hi, d.lo);
+      }
+  if ((e = cudaMemcpyAsync(b->st, st.data(), st.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b->Xs, 0, static_cast<size_t>(b->Rpad) * 2 * b->Kpad * 2, s)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  sto::sweep_publish_kernel<<<static_cast<unsigned>((RN + 255) / 256), 256, 0, s>>>(
+      b->st + 3 * RN, b->Xs, static_cast<int>(N), R, b->Kpad);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sto::sweep_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sto::kSwSmem)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  *out = b;
+  return STO_OK;
+}
+
+int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out) {
+  if (!b || T < 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  if (!u) return STO_EINVAL;
+  const sto_params& P = b->params;
+  cudaStream_t s = b->stream;
+  const size_t n_u = static_cast<size_t>(T) * P.n_in;
+  const size_t n_states = static_cast<size_t>(T) * b->R * b->N;
+  int rc = grow(&b->d_u, &b->d_u_cap, n_u);
+  if (rc) return rc;
+  STO_CUDA(cudaMemcpyAsync(b->d_u, u, n_u * 4, cudaMemcpyDefault, s));
+  float* d_states = states_out;
+  const bool host_states = states_out && !is_device_ptr(states_out);
+  if (host_states) {
+    rc = grow(&b->d_states, &b->d_states_cap, n_states);
+    if (rc) return rc;
+    d_states = b->d_states;
+  }
+  STO_CUDA(cudaMemsetAsync(b->t_dev, 0, 4, s));
+  STO_CUDA(cudaMemsetAsync(b->d_err, 0, 16, s));
+  // the sweep runs on its own stream, ordered after the caller's work
+  STO_CUDA(cudaEventRecord(b->ev, s));
+  STO_CUDA(cudaStreamWaitEvent(b->own, b->ev, 0));
+  // one input sample as a CUDA graph, replayed T times
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  STO_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+  rc = batch_enqueue_sample(b, b->d_u, d_states);
+  const cudaError_t ce = cudaStreamEndCapture(b->own, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) {
+    for (int64_t t = 0; t < T && e == cudaSuccess; ++t) e = cudaGraphLaunch(exec, b->own);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->own);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && host_states)
+    e = cudaMemcpyAsync(states_out, d_states, n_states * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (b->h_err[0] != 0) return b->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  return STO_OK;
+}
+
+int sto_batch_get_state(const sto_batch* b, double* m) {
+  if (!b || !m) return STO_EINVAL;
+  const size_t RN = static_cast<size_t>(b->R) * b->N;
+  std::vector<float2> mn(3 * RN);
+  STO_CUDA(cudaMemcpyAsync(mn.data(), b->st, 3 * RN * sizeof(float2), cudaMemcpyDeviceToHost, b->stream));
+  STO_CUDA(cudaStreamSynchronize(b->stream));
+  std::vector<double> out(3 * RN);
+  for (int r = 0; r < b->R; ++r)
+    for (int i = 0; i < 3; ++i)
+      for (int64_t k = 0; k < b->N; ++k) {
+        const float2 v = mn[i * RN + static_cast<size_t>(r) * b->N + k];
+        out[(static_cast<size_t>(r) * 3 + i) * b->N + k] = static_cast<double>(v.x) + v.y;
+      }
+  STO_CUDA(cudaMemcpyAsync(m, out.data(), out.size() * 8, cudaMemcpyDefault, b->stream));
+  STO_CUDA(cudaStreamSynchronize(b->stream));
+  return STO_OK;
+}
+
+void sto_batch_destroy(sto_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
 }
 
 }  // extern "C"

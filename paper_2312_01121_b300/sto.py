@@ -86,6 +86,11 @@ SIGNATURES = {
                                        _I64, _VP, _VP]),
     "sto_adjoint": (ctypes.c_int, [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sto_grads)]),
     "sto_set_input_weights": (ctypes.c_int, [_VP, _VP]),
+    "sto_batch_create": (ctypes.c_int, [_I64, _I32, ctypes.POINTER(sto_params), _VP, _VP, _VP,
+                                        _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "sto_run_batched": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "sto_batch_get_state": (ctypes.c_int, [_VP, _VP]),
+    "sto_batch_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -348,6 +353,60 @@ class Reservoir:
     def close(self):
         if self.handle:
             sto_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Sweep:
+    """R reservoirs sharing W (rounded to BF16), with per-reservoir current and
+    input gain, advanced together (tensor-core coupling product per stage)."""
+
+    def __init__(self, W, w_in, params: Params, currents=None, gains=None, m0=None, stream=None):
+        lib = load_library()
+        self.N = int(W.shape[0])
+        self.params = params
+        self.R = int(len(currents)) if currents is not None else int(len(gains))
+        cur = np.ascontiguousarray(currents, dtype=np.float64) if currents is not None else None
+        gn = np.ascontiguousarray(gains, dtype=np.float64) if gains is not None else None
+        pW, kW = _ptr(W, np.float32)
+        pwin, kwin = _ptr(w_in, np.float32)
+        pm0, km0 = _ptr(m0, np.float32)
+        h = _VP()
+        cp = params.to_c()
+        _check(lib.sto_batch_create(self.N, self.R, ctypes.byref(cp),
+                                    cur.ctypes.data if cur is not None else None,
+                                    gn.ctypes.data if gn is not None else None,
+                                    pW, pwin, pm0, _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h.value
+
+    def run(self, u, states_out=None, T=None):
+        """states_out: T x R x N float32 (numpy or torch) or None."""
+        if T is None:
+            T = int(u.shape[0])
+        pu, ku = _ptr(u, np.float32)
+        ps, ks = _ptr(states_out, np.float32)
+        _check(load_library().sto_run_batched(self.handle, pu, T, ps))
+        return states_out
+
+    def state(self) -> np.ndarray:
+        out = np.empty((self.R, 3, self.N), dtype=np.float64)
+        _check(load_library().sto_batch_get_state(self.handle, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.handle:
+            load_library().sto_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
