@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-n", type=int, default=2500)
+    ap.add_argument("--sweep-r", type=int, default=512)
+    ap.add_argument("--sweep-t", type=int, default=2, help="input samples per timed sweep call")
     ap.add_argument("--adj-n", type=int, default=1000)
     ap.add_argument("--adj-t", type=int, default=40, help="input samples per adjoint call")
     ap.add_argument("--adj-k", type=int, default=20, help="checkpoint interval (samples)")
@@ -101,6 +105,17 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"bf16": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "source": "measured"}
+    except Exception:
+        return {"bf16": 1800.0, "bf16_sustained": 1400.0, "source": "fallback"}
 
 
 class ClockSampler:
@@ -262,6 +277,52 @@ def time_adjoint(args, seed, torch, sto, dev):
                     "one call = checkpoint pass + recomputation with recording + reverse pass"}
 
 
+def time_sweep(args, seed, torch, sto, dev, peaks):
+    """sto_run_batched: R reservoirs sharing one N x N Gaussian W, currents
+    I ~ U[1, 3] mA and input gains g ~ U[0.5, 2] (one per reservoir), the same
+    u ~ U[0, 1] for all; states of every reservoir sampled every input sample."""
+    N, R, T = args.sweep_n, args.sweep_r, args.sweep_t
+    W, w_in, _, u = workload(N, T * 4, seed)
+    rng = np.random.default_rng([seed, 7])
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    m0 = np.ascontiguousarray(np.stack([workload(N, 1, seed + 1000 + r)[2] for r in range(min(R, 8))]
+                                       * ((R + 7) // 8))[:R])
+    P = sto.Params(substeps=args.substeps)
+    sw = sto.Sweep(torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), P, currents=cur,
+                   gains=gain, m0=torch.from_numpy(m0).to(dev), stream=torch.cuda.current_stream())
+    u_d = torch.from_numpy(u).to(dev)
+    st = torch.empty((T, R, N), dtype=torch.float32, device=dev)
+    sw.run(u_d[:T], st)  # warm-up: graph capture path, caches
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for i in range(reps):
+        sw.run(u_d[T * (i + 1):T * (i + 2)], st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    finite = bool(torch.isfinite(st).all().item())
+    sw.close()
+    stages = 4 * args.substeps * T
+    us_stage = ms * 1e3 / stages
+    Mpad, Kpad, Rpad = -(-N // 128) * 128, -(-N // 64) * 64, -(-R // 64) * 64
+    alg_flop = 2.0 * N * N * R            # the coupling product W X of one stage
+    exe_flop = 2.0 * Mpad * (2 * Kpad) * Rpad  # executed: hi/lo split, padded tiles
+    return {"workload": f"{R} reservoirs sharing one N={N} Gaussian W (BF16), I~U[1,3] mA, "
+                        f"g~U[0.5,2], u~U[0,1]; {T} input samples x {args.substeps} RK4 steps per call",
+            "value": R * N * args.substeps * T / (ms / 1e3), "unit": "node-updates/s",
+            "ms_per_call": ms, "us_per_stage": us_stage,
+            "coupling_tflops_algorithmic": alg_flop / (us_stage * 1e-6) / 1e12,
+            "coupling_tflops_executed": exe_flop / (us_stage * 1e-6) / 1e12,
+            "tensor_peak_tflops": peaks.get("bf16"),
+            "frac_of_bf16_peak_whole_stage": (exe_flop / (us_stage * 1e-6) / 1e12) / peaks["bf16"]
+            if peaks.get("bf16") else None,
+            "finite": finite}
+
+
 def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
     """Node-updates/s of the FP64 oracle on a bounded sample of the workload."""
     import oracle
@@ -348,6 +409,9 @@ def main():
     adj = None
     if not args.no_adjoint:
         adj = time_adjoint(args, replica_seed(rank), torch, sto, dev)
+    sweep = None
+    if not args.no_sweep:
+        sweep = time_sweep(args, replica_seed(rank), torch, sto, dev, measured_bf16())
 
     value, e2e_value, tot_ms, updates = combine_ranks(
         main_r["total_ms"], main_r.get("e2e_s"), main_r["node_updates"], world, reduce_max)
@@ -432,6 +496,8 @@ def main():
         }
     if adj is not None:
         line["adjoint"] = adj
+    if sweep is not None:
+        line["sweep"] = sweep
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
