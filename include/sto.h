@@ -210,6 +210,18 @@ typedef struct sto_grads {
 STO_API int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstates,
                         int32_t ckpt_every, sto_grads* out);
 
+/* Advance n independent reservoirs (each its own handle: its own W, N,
+ * parameters and launch plan) over the same input series u (T x n_in, host
+ * or device; every handle must have the same n_in and device).  The n
+ * persistent launches are captured into one CUDA graph and run back to
+ * back; states_out[i] (T x N_i, host or device, or NULL; states_out itself may
+ * be NULL) receives reservoir i's states.  The uneven-N, own-W half of a
+ * parameter sweep.
+ * Errors: STO_EINVAL (duplicate handles, mismatched n_in), STO_ENOMEM,
+ *         STO_ETIMEOUT, STO_ECUDA, STO_ENOTSUP. */
+STO_API int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
+                          float* const* states_out);
+
 /* Replace the input weights w_in (N x n_in float32, host or device).
  * Errors: STO_EINVAL, STO_ENONFINITE, STO_ECUDA. */
 STO_API int sto_set_input_weights(sto_handle* h, const float* w_in);

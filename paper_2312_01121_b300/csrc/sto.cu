@@ -394,17 +394,23 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   return a;
 }
 
-// Enqueue one forward launch (optionally recording the trajectory).
-int engine_launch(sto_handle* h, const float* d_u, int64_t T, float* d_states,
-                  float2* rec_m, float* rec_h) {
+// Enqueue one forward launch (optionally recording the trajectory) on
+// stream s (the handle's own stream unless a group capture passes another).
+int engine_launch_on(sto_handle* h, cudaStream_t s, const float* d_u, int64_t T, float* d_states,
+                     float2* rec_m, float* rec_h) {
   sto::KArgs a = base_args(h, d_u, T);
   a.states_out = d_states;
   a.rec_m = rec_m;
   a.rec_h = rec_h;
-  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, h->stream));
-  STO_CUDA(launch_stepper(h->plan, a, h->stream));
-  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, h->stream));
+  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
+  STO_CUDA(launch_stepper(h->plan, a, s));
+  STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s));
   return STO_OK;
+}
+
+int engine_launch(sto_handle* h, const float* d_u, int64_t T, float* d_states, float2* rec_m,
+                  float* rec_h) {
+  return engine_launch_on(h, h->stream, d_u, T, d_states, rec_m, rec_h);
 }
 
 // Enqueue one adjoint launch over a recorded segment of T samples.
@@ -810,6 +816,88 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
   }
   if (out->dm0) STO_CUDA(cudaMemcpyAsync(out->dm0, lam.data(), n3 * 8, cudaMemcpyDefault, s));
   STO_CUDA(cudaStreamSynchronize(s));
+  return STO_OK;
+}
+
+int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
+                  float* const* states_out) {
+  if (!hs || n < 1 || T < 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  if (!u) return STO_EINVAL;
+  sto_handle* h0 = hs[0];
+  if (!h0) return STO_EINVAL;
+  const int n_in = h0->params.n_in;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || hs[i]->params.n_in != n_in || hs[i]->device != h0->device) return STO_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return STO_EINVAL;
+    const uint64_t stages = 4ULL * static_cast<uint64_t>(hs[i]->params.substeps) * static_cast<uint64_t>(T);
+    if (stages > 0x40000000ULL) return STO_ENOTSUP;
+  }
+  if (T > (1LL << 31) - 1) return STO_ENOTSUP;
+  cudaStream_t s0 = h0->stream;
+  // the shared input, staged once
+  const size_t n_u = static_cast<size_t>(T) * n_in;
+  const float* d_u = u;
+  if (!is_device_ptr(u)) {
+    int rc = grow(&h0->d_u, &h0->d_u_cap, n_u);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(h0->d_u, u, n_u * 4, cudaMemcpyHostToDevice, s0));
+    d_u = h0->d_u;
+  }
+  std::vector<float*> d_states(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    float* so = states_out ? states_out[i] : nullptr;
+    d_states[i] = so;
+    if (so && !is_device_ptr(so)) {
+      int rc = grow(&hs[i]->d_states, &hs[i]->d_states_cap, static_cast<size_t>(T) * hs[i]->N);
+      if (rc) return rc;
+      d_states[i] = hs[i]->d_states;
+    }
+  }
+  // every reservoir's persistent launch, in order, as one CUDA graph
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  STO_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(ev, hs[i]->stream);  // after each handle's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = STO_OK;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < n && !rc; ++i) rc = engine_launch_on(hs[i], cs, d_u, T, d_states[i], nullptr, nullptr);
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (!rc && ce != cudaSuccess) rc = cuda_fail(ce);
+  } else {
+    rc = cuda_fail(e);
+  }
+  if (!rc) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      float* so = states_out ? states_out[i] : nullptr;
+      if (so && so != d_states[i])
+        e = cudaMemcpyAsync(so, d_states[i], static_cast<size_t>(T) * hs[i]->N * 4,
+                            cudaMemcpyDeviceToHost, cs);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(cs);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    hs[i]->inject_cta = -1;
+    if (hs[i]->h_err[0] != 0) return hs[i]->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  }
   return STO_OK;
 }
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "sto_run_batched": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "sto_batch_get_state": (ctypes.c_int, [_VP, _VP]),
     "sto_batch_destroy": (None, [_VP]),
+    "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
 }
 
 _lib = None
@@ -261,6 +262,26 @@ def sto_adjoint(h, u, T, dL_dstates, ckpt_every=100, dw_in=None, dm0=None) -> di
 def sto_set_input_weights(h, w_in):
     p, k = _ptr(w_in, np.float32)
     _check(load_library().sto_set_input_weights(h, p))
+
+
+def sto_run_group(reservoirs, u, T=None, states_out=None):
+    """Advance several Reservoir objects (own W, uneven N) over the same u in
+    one graph-captured sequence of persistent launches."""
+    n = len(reservoirs)
+    if T is None:
+        T = int(u.shape[0])
+    hs = (_VP * n)(*[r.handle for r in reservoirs])
+    pu, ku = _ptr(u, np.float32)
+    keep = []
+    outs = None
+    if states_out is not None:
+        ptrs = []
+        for so in states_out:
+            p, k = _ptr(so, np.float32)
+            ptrs.append(p)
+            keep.append(k)
+        outs = (_VP * n)(*ptrs)
+    _check(load_library().sto_run_group(hs, n, pu, T, outs))
 
 
 def sto_get_info(h) -> dict:

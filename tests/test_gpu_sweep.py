@@ -89,3 +89,29 @@ def test_sweep_resumes_across_calls(sto):
         sw.run(u[:2], b1)
         sw.run(u[2:], b2)
     assert np.array_equal(np.concatenate([b1, b2]), a)
+
+
+def test_group_of_own_w_reservoirs_matches_separate_runs(sto):
+    """Reservoirs with their own W and uneven N in one graph-captured call
+    give the same bits as separate sto_run calls, and match the oracle."""
+    Ns = [100, 333, 1000, 2049, 4000]
+    T = 2
+    u = make_system(4, "gauss", seed=1, T=T)[3]
+    systems = [make_system(N, "gauss", seed=20 + i, T=T) for i, N in enumerate(Ns)]
+    params = [sto.Params(substeps=4, current=1e-3 + 4e-4 * i, A_cp=30.0) for i in range(len(Ns))]
+    grp = [sto.Reservoir(W, w_in, P, m0=m0) for (W, w_in, m0, _), P in zip(systems, params)]
+    outs = [np.zeros((T, N), np.float32) for N in Ns]
+    sto.sto_run_group(grp, u, T, outs)
+    ends = [r.state() for r in grp]
+    for r in grp:
+        r.close()
+    for (W, w_in, m0, _), P, o, e in zip(systems, params, outs, ends):
+        ref = np.zeros_like(o)
+        with sto.Reservoir(W, w_in, P, m0=m0) as r:
+            r.run(u, ref)
+            assert np.array_equal(r.state(), e)
+        assert np.array_equal(o, ref)
+    W, w_in, m0, _ = systems[0]
+    _, orc = oracle.run(oracle_params(params[0]), W.astype(np.float64), w_in.astype(np.float64),
+                        m0.astype(np.float64), u.astype(np.float64))
+    assert np.max(np.abs(outs[0] - orc)) <= 1e-5
