@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--l2-keep-mb", type=int, default=0)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-n", type=int, default=2500)
@@ -196,7 +197,8 @@ def time_device(N, args, ips, seed, torch, sto, dev):
     stream = torch.cuda.current_stream()
     Wd = torch.from_numpy(W).to(dev)
     res = sto.Reservoir(Wd, torch.from_numpy(w_in).to(dev), P,
-                        m0=torch.from_numpy(m0).to(dev), stream=stream, grid=args.grid)
+                        m0=torch.from_numpy(m0).to(dev), stream=stream, grid=args.grid,
+                        l2_keep_mb=args.l2_keep_mb)
     del Wd
     torch.cuda.empty_cache()
     info = res.info()

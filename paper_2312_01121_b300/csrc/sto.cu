@@ -151,6 +151,7 @@ struct sto_handle {
   sto_params params{};
   Plan plan;
   int timeout_ms = kDefaultTimeoutMs;
+  int l2_keep_mb = 0;
   int inject_cta = -1;
   uint64_t stage_counter = 0;
   float* d_W = nullptr;
@@ -297,6 +298,16 @@ int grow(float** buf, size_t* cap, size_t n) {
 // streamed from HBM with evict_first so that it does not flush the rest.
 int l2_keeps(int64_t N) { return 4.0 * static_cast<double>(N) * N <= 96.0 * (1 << 20) ? 1 : 0; }
 
+// Leading panels of every row block to keep L2-resident when W is larger
+// than L2: a `mb` megabyte slice of W (default 80 MB of the 126 MB L2).
+int keep_panels(int64_t N, int P, int mb) {
+  if (mb < 0 || l2_keeps(N)) return 0;
+  const double budget = (mb == 0 ? 80.0 : static_cast<double>(mb)) * (1 << 20);
+  const double wbytes = 4.0 * static_cast<double>(N) * N;
+  const int k = static_cast<int>(P * budget / wbytes);
+  return k < P ? k : P;
+}
+
 // Constants of Eq. (gov) in the form the stepper uses.
 void set_constants(const sto_params& P, sto::KArgs* a) {
   using sto::df_split_host;
@@ -381,6 +392,7 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   a.inject_cta = h->inject_cta;
   a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
   a.l2_keep = l2_keeps(h->N);
+  a.keep_panels = keep_panels(h->N, h->plan.P, h->l2_keep_mb);
   set_constants(P, &a);
   // tags [base, base + stages] are fresh: none was written before
   const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
@@ -503,8 +515,8 @@ int sto_create_ex(int64_t N, const sto_params* params, const float* W, const flo
   int rc = check_params(params);
   if (rc) return rc;
   if (cfg) {
-    if (cfg->grid < 0 || cfg->timeout_ms < 0) return STO_EINVAL;
-    for (int i = 0; i < 6; ++i)
+    if (cfg->grid < 0 || cfg->timeout_ms < 0 || cfg->l2_keep_mb < -1) return STO_EINVAL;
+    for (int i = 0; i < 5; ++i)
       if (cfg->reserved[i] != 0) return STO_EINVAL;
   }
   if (N > (1LL << 20)) return STO_ENOTSUP;
@@ -515,6 +527,7 @@ int sto_create_ex(int64_t N, const sto_params* params, const float* W, const flo
   h->params = *params;
   h->stream = static_cast<cudaStream_t>(stream);
   if (cfg && cfg->timeout_ms > 0) h->timeout_ms = cfg->timeout_ms;
+  if (cfg) h->l2_keep_mb = cfg->l2_keep_mb;
 
   auto fail = [&](int code) {
     if (h->stream) cudaStreamSynchronize(h->stream);

@@ -55,6 +55,7 @@ struct KArgs {
   int* err;                  // int32[4]
   int N, n_in, T, S, P, ns, resident, comp, inject_cta;
   int l2_keep;               // W small enough to stay in L2 between stages
+  int keep_panels;           // otherwise: leading panels of each row block kept in L2
   unsigned int tag_base;
   unsigned long long timeout_ns;
   // constants of Eq. (gov) as double-float pairs
@@ -673,7 +674,11 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   }
   if (warp == kConsWarps) {
     if (lane == 0) {
-      const uint64_t pol = (a.resident || a.l2_keep) ? policy_evict_last() : policy_evict_first();
+      // W that fits in L2 stays there (evict_last); larger W keeps its
+      // leading keep_panels panels of every row block in L2 and streams the
+      // rest from HBM (evict_first), so that part is not re-read from DRAM
+      const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+      const bool all_keep = a.resident || a.l2_keep;
       const long long total =
           a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
       long long it = 0;
@@ -689,7 +694,8 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
         }
         mbar_arrive_expect_tx(&full[slot], panel_bytes);
         bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats,
-                 Wc + static_cast<size_t>(j) * R * kPanelCols, panel_bytes, &full[slot], pol);
+                 Wc + static_cast<size_t>(j) * R * kPanelCols, panel_bytes, &full[slot],
+                 (all_keep || j < a.keep_panels) ? keep : stream);
         if (++j == a.P) j = 0;
         if (++slot == a.ns) {
           slot = 0;

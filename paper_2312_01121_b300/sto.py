@@ -44,7 +44,7 @@ class sto_params(ctypes.Structure):
 
 class sto_config(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("l2_keep_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class sto_info(ctypes.Structure):
@@ -187,7 +187,8 @@ def _stream_ptr(stream):
     return int(stream)
 
 
-def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout_ms=0):
+def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout_ms=0,
+               l2_keep_mb=0):
     """Returns an opaque handle (int).  W, w_in, m0: numpy or torch float32."""
     lib = load_library()
     pW, kW = _ptr(W, np.float32)
@@ -195,8 +196,8 @@ def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout
     pm0, km0 = _ptr(m0, np.float32)
     h = _VP()
     cp = params.to_c()
-    if grid or timeout_ms:
-        cfg = sto_config(grid=grid, timeout_ms=timeout_ms)
+    if grid or timeout_ms or l2_keep_mb:
+        cfg = sto_config(grid=grid, timeout_ms=timeout_ms, l2_keep_mb=l2_keep_mb)
         rc = lib.sto_create_ex(N, ctypes.byref(cp), pW, pwin, pm0, _stream_ptr(stream),
                                ctypes.byref(cfg), ctypes.byref(h))
     else:
@@ -322,10 +323,11 @@ class Reservoir:
     """One reservoir of N coupled STOs on the current CUDA device."""
 
     def __init__(self, W, w_in, params: Params | None = None, m0=None, stream=None,
-                 grid: int = 0, timeout_ms: int = 0):
+                 grid: int = 0, timeout_ms: int = 0, l2_keep_mb: int = 0):
         self.params = params or Params()
         self.N = int(W.shape[0])
-        self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms)
+        self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms,
+                                 l2_keep_mb)
 
     def run(self, u, states_out=None, T=None):
         """Advance over T = len(u) input samples; fills states_out (T x N) if given."""
