@@ -16,6 +16,8 @@ Parity status of each function (the pins are in ``tests/test_oracle_pins.py``):
                  closed-form trajectories, norm drift O(dt^4)
   initial_state  pinned: Eq. (initial) unit norm and the stated limit (0,0,1)
   readout        pinned: ridge at beta -> 0 equals numpy lstsq
+  erk            pinned: local error order p+1 of Euler, Heun, Kutta-3 and RK4
+                 tableaus against DOP853; the RK4 tableau reproduces `run`
   adjoint        pinned: central finite differences of `run` (FP64) for A_cp,
                  I, w_in and m0, including the refitted-readout objective
                  (tests/test_oracle_adjoint.py)
@@ -127,6 +129,10 @@ def _load():
             lib.orc_adjoint.argtypes = [ctypes.c_int, P, D, D, D, D, ctypes.c_int, D, D,
                                         ctypes.c_int]
             lib.orc_adjoint.restype = ctypes.c_int
+            lib.orc_erk_step.argtypes = [ctypes.c_int, P, D, D, D, ctypes.c_int, D, D, ctypes.c_int]
+            lib.orc_run_erk.argtypes = [ctypes.c_int, P, D, D, D, D, ctypes.c_int, D, ctypes.c_int,
+                                        D, D, ctypes.c_int]
+            lib.orc_run_erk.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -255,3 +261,53 @@ def adjoint(params: OracleParams, W, w_in, m0, u, dL_dstates, nthreads: int = 1)
     nw = N * params.n_in
     return {"A_cp": out[0], "current": out[1], "w_in": out[2:2 + nw].reshape(N, params.n_in),
             "m0": out[2 + nw:].reshape(3, N)}
+
+
+# Explicit Runge-Kutta tableaus (a strictly lower triangular, weights b).
+TABLEAUS = {
+    "euler": ([[0.0]], [1.0]),
+    "heun": ([[0.0, 0.0], [1.0, 0.0]], [0.5, 0.5]),
+    "kutta3": ([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [-1.0, 2.0, 0.0]], [1 / 6, 2 / 3, 1 / 6]),
+    "rk4": ([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0, 1.0, 0]],
+            [1 / 6, 1 / 3, 1 / 3, 1 / 6]),
+    # Kutta's 3/8 rule: order 4 with every entry below the diagonal in use
+    "rk38": ([[0, 0, 0, 0], [1 / 3, 0, 0, 0], [-1 / 3, 1.0, 0, 0], [1.0, -1.0, 1.0, 0]],
+             [1 / 8, 3 / 8, 3 / 8, 1 / 8]),
+}
+
+
+def erk_step(params: OracleParams, W, m, a, b, hin=None, nthreads: int = 1) -> np.ndarray:
+    W = _f64(W)
+    N = W.shape[0]
+    m = _f64(m, (3, N)).copy()
+    s = len(b)
+    A = _f64(a, (s, s))
+    B = _f64(b, (s,))
+    hin_a = _f64(hin, (N,)) if hin is not None else np.zeros(N)
+    c = params._c()
+    _load().orc_erk_step(N, ctypes.byref(c), _d(W), _d(hin_a), _d(m), s, _d(A), _d(B), nthreads)
+    return m
+
+
+def run_erk(params: OracleParams, W, w_in, m0, u, a, b, T: int | None = None, nthreads: int = 1):
+    """`run` with an explicit Runge-Kutta tableau in place of classic RK4."""
+    W = _f64(W)
+    N = W.shape[0]
+    u = _f64(u)
+    if u.ndim == 1:
+        u = u.reshape(-1, 1)
+    if T is None:
+        T = u.shape[0]
+    u = np.ascontiguousarray(u[:T].reshape(T, params.n_in)) if T > 0 else np.zeros((1, params.n_in))
+    w_in = _f64(w_in).reshape(N, params.n_in)
+    m = _f64(m0, (3, N)).copy()
+    s = len(b)
+    A = _f64(a, (s, s))
+    B = _f64(b, (s,))
+    states = np.zeros((max(T, 1), N))
+    c = params._c()
+    rc = _load().orc_run_erk(N, ctypes.byref(c), _d(W), _d(w_in), _d(m), _d(u), T, _d(states),
+                             s, _d(A), _d(B), nthreads)
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return m, states[:T]

@@ -385,3 +385,50 @@ int orc_adjoint(int N, const orc_params* P, const double* W, const double* w_in,
   for (int q = 0; q < 4; ++q) free(yb[q]);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * General explicit Runge-Kutta stepping (the paper's closing claim: the
+ * approach applies to any reservoir evolved by an explicit method).  An
+ * s-stage explicit tableau (a strictly lower triangular, weights b):
+ *     k_i = f(m + dt sum_{j<i} a[i][j] k_j),   m' = m + dt sum_i b[i] k_i.
+ * The input field is held over the step, as for RK4.
+ * ------------------------------------------------------------------------ */
+void orc_erk_step(int N, const orc_params* P, const double* W, const double* hin, double* m,
+                  int s, const double* a, const double* b, int nthreads) {
+  size_t n3 = 3 * (size_t)N;
+  double* k = (double*)malloc(sizeof(double) * n3 * (size_t)s);
+  double* y = (double*)malloc(sizeof(double) * n3);
+  for (int i = 0; i < s; ++i) {
+    for (size_t q = 0; q < n3; ++q) {
+      double acc = 0.0;
+      for (int j = 0; j < i; ++j) acc += a[i * s + j] * k[(size_t)j * n3 + q];
+      y[q] = m[q] + P->dt * acc;
+    }
+    orc_field(N, P, W, y, hin, k + (size_t)i * n3, NULL, nthreads);
+  }
+  for (size_t q = 0; q < n3; ++q) {
+    double acc = 0.0;
+    for (int i = 0; i < s; ++i) acc += b[i] * k[(size_t)i * n3 + q];
+    m[q] += P->dt * acc;
+  }
+  free(k);
+  free(y);
+}
+
+/* orc_run with an explicit tableau in place of classic RK4. */
+int orc_run_erk(int N, const orc_params* P, const double* W, const double* w_in, double* m,
+                const double* u, int T, double* states, int s, const double* a, const double* b,
+                int nthreads) {
+  if (N < 1 || T < 0 || !P || !W || !m || (T > 0 && (!u || !w_in)) || s < 1 || s > 8 ||
+      !a || !b || P->substeps < 1 || P->n_in < 1 || P->component < 0 || P->component > 2)
+    return -1;
+  double* hin = (double*)malloc(sizeof(double) * (size_t)N);
+  for (int t = 0; t < T; ++t) {
+    orc_input_field(N, P, w_in, u + (size_t)t * P->n_in, hin);
+    for (int q = 0; q < P->substeps; ++q) orc_erk_step(N, P, W, hin, m, s, a, b, nthreads);
+    if (states)
+      for (int k = 0; k < N; ++k) states[(size_t)t * N + k] = m[(size_t)P->component * N + k];
+  }
+  free(hin);
+  return 0;
+}
