@@ -122,6 +122,39 @@ def measured_bf16():
         return {"bf16": 1800.0, "bf16_sustained": 1400.0, "source": "fallback"}
 
 
+# Sources whose change invalidates a recorded DRAM-traffic figure of the
+# stepper kernel (device code and the host code that plans its launch).
+STEPPER_SOURCES = ("paper_2312_01121_b300/csrc/sto_kernel.cuh", "paper_2312_01121_b300/csrc/dfloat.cuh",
+                   "paper_2312_01121_b300/csrc/sto.cu", "include/sto.h")
+TRAFFIC_FILE = os.path.join("profiles", "dram_traffic.txt")
+
+
+def stepper_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in STEPPER_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(N: int, stages: int):
+    """DRAM bytes (read + write) of one stepper launch of `stages` stages at N,
+    from the steady per-stage figure an ncu capture recorded, or None when no
+    capture of the current kernel sources at this N exists."""
+    try:
+        digest = stepper_source_digest()
+        with open(os.path.join(ROOT, TRAFFIC_FILE)) as fh:
+            for line in fh:
+                f = line.split()
+                if len(f) >= 4 and not f[0].startswith("#") and f[0] == "sto_persistent_kernel" \
+                        and int(f[1]) == N and f[2] == digest:
+                    return float(f[3]) * stages
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 50 ms; only the
     samples taken between mark_start() and mark_end() are summarised."""
@@ -493,8 +526,8 @@ def main():
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "dtype_detail": "FP32 W and coupling matvec (FP32 accumulate); FP64 per-oscillator "
-                        "torque, RK4 combine and state",
+        "dtype_detail": "FP32 W and coupling matvec (FP32 accumulate); double-float (two FP32, "
+                        "~48-bit) per-oscillator torque and RK4 combine; FP64 state between calls",
         "data": "synthetic",
         "config": {
             "workload": f"plain single reservoir, N={N}, dense Gaussian FP32 W (std 0.1/sqrt(N), "
@@ -506,7 +539,8 @@ def main():
             "plan": main_r["info"],
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak, "traffic": recorded_traffic(N, stages),
+                     "peak_source": peak_kind,
                      "kernel": "sto_persistent_kernel",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3,

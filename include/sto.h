@@ -224,6 +224,16 @@ STO_API int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* d
 STO_API int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
                           float* const* states_out);
 
+/* Use an explicit Runge-Kutta method other than classic RK4 (Sec. 3.2 uses
+ * classic RK4; the paper's conclusion notes that the approach applies to
+ * any reservoir evolved by an explicit method).  stages = s in 1..4;
+ * a: s x s row-major Butcher matrix, strictly lower triangular (entries on
+ * or above the diagonal must be 0); b: s weights.  stages = 0 (a, b NULL)
+ * restores classic RK4.  Each RK step then takes s exchange stages.  The
+ * adjoint (sto_adjoint) is available for classic RK4 only (STO_ENOTSUP).
+ * Errors: STO_EINVAL (implicit or non-finite tableau, s out of range). */
+STO_API int sto_set_tableau(sto_handle* h, int32_t stages, const double* a, const double* b);
+
 /* Replace the input weights w_in (N x n_in float32, host or device).
  * Errors: STO_EINVAL, STO_ENONFINITE, STO_ECUDA. */
 STO_API int sto_set_input_weights(sto_handle* h, const float* w_in);

@@ -152,6 +152,10 @@ struct sto_handle {
   Plan plan;
   int timeout_ms = kDefaultTimeoutMs;
   int l2_keep_mb = 0;
+  int rk_stages = 4;           // explicit tableau; classic RK4 unless set
+  bool rk_classic = true;
+  double rk_a[16] = {};
+  double rk_b[4] = {};
   int inject_cta = -1;
   uint64_t stage_counter = 0;
   float* d_W = nullptr;
@@ -197,11 +201,29 @@ void free_handle(sto_handle* h) {
   delete h;
 }
 
-template <int RPW, bool kRowMajorW = false, bool kAdjoint = false>
+// The device's opt-in shared-memory limit per block.  The kernels' dynamic
+// shared-memory cap is set to it, not to one plan's size: handles of
+// different N share the function, and a captured graph (sto_run_group) holds
+// launches of several sizes, so a per-launch cap would leave the last one set
+// below what an earlier launch in the graph asks for.
+int smem_optin_limit() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+      cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW, kAdjoint>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(pl.smem));
+  const int cap = smem_optin_limit();
+  if (cap < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.G);
@@ -213,7 +235,7 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kAdjoint>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>, a);
 }
 
 cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -225,11 +247,21 @@ cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStr
 }
 
 cudaError_t launch_adjoint(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  if (pl.rpw <= 1) return launch_rpw<1, false, true>(pl, a, s);
-  if (pl.rpw <= 2) return launch_rpw<2, false, true>(pl, a, s);
-  if (pl.rpw <= 4) return launch_rpw<4, false, true>(pl, a, s);
-  if (pl.rpw <= 8) return launch_rpw<8, false, true>(pl, a, s);
-  return launch_rpw<16, false, true>(pl, a, s);
+  constexpr int A = sto::kProgAdjoint;
+  if (pl.rpw <= 1) return launch_rpw<1, false, A>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2, false, A>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4, false, A>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8, false, A>(pl, a, s);
+  return launch_rpw<16, false, A>(pl, a, s);
+}
+
+cudaError_t launch_tableau(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  constexpr int B = sto::kProgTableau;
+  if (pl.rpw <= 1) return launch_rpw<1, false, B>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2, false, B>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4, false, B>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8, false, B>(pl, a, s);
+  return launch_rpw<16, false, B>(pl, a, s);
 }
 
 cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -394,8 +426,15 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   a.l2_keep = l2_keeps(h->N);
   a.keep_panels = keep_panels(h->N, h->plan.P, h->l2_keep_mb);
   set_constants(P, &a);
+  a.rk_stages = h->rk_stages;
+  for (int i = 0; i < 4; ++i) {
+    a.rk_b[i] = sto::df_split_host(i < h->rk_stages ? h->rk_b[i] : 0.0);
+    for (int j = 0; j < 4; ++j)
+      a.rk_a[i][j] = sto::df_split_host(i < h->rk_stages && j < i ? h->rk_a[i * 4 + j] : 0.0);
+  }
   // tags [base, base + stages] are fresh: none was written before
-  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  const uint64_t stages = static_cast<uint64_t>(h->rk_stages) * static_cast<uint64_t>(P.substeps) *
+                          static_cast<uint64_t>(T);
   if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
     cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(h->N) * 8, h->stream);
     h->stage_counter = 0;
@@ -415,7 +454,10 @@ int engine_launch_on(sto_handle* h, cudaStream_t s, const float* d_u, int64_t T,
   a.rec_m = rec_m;
   a.rec_h = rec_h;
   STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
-  STO_CUDA(launch_stepper(h->plan, a, s));
+  if (h->rk_classic)
+    STO_CUDA(launch_stepper(h->plan, a, s));
+  else
+    STO_CUDA(launch_tableau(h->plan, a, s));
   STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s));
   return STO_OK;
 }
@@ -711,7 +753,8 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
   if (T == 0) return STO_OK;
   if (!u) return STO_EINVAL;
   const sto_params& P = h->params;
-  const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
+  const uint64_t stages = static_cast<uint64_t>(h->rk_stages) * static_cast<uint64_t>(P.substeps) *
+                          static_cast<uint64_t>(T);
   if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
   const int64_t N = h->N;
   cudaStream_t s = h->stream;
@@ -742,6 +785,7 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
 int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstates,
                 int32_t ckpt_every, sto_grads* out) {
   if (!h || T < 1 || !u || !dL_dstates || !out || ckpt_every < 1) return STO_EINVAL;
+  if (!h->rk_classic) return STO_ENOTSUP;  // the adjoint is that of classic RK4
   const sto_params& P = h->params;
   const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
   if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
@@ -844,7 +888,8 @@ int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
     if (!hs[i] || hs[i]->params.n_in != n_in || hs[i]->device != h0->device) return STO_EINVAL;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return STO_EINVAL;
-    const uint64_t stages = 4ULL * static_cast<uint64_t>(hs[i]->params.substeps) * static_cast<uint64_t>(T);
+    const uint64_t stages = static_cast<uint64_t>(hs[i]->rk_stages) *
+                            static_cast<uint64_t>(hs[i]->params.substeps) * static_cast<uint64_t>(T);
     if (stages > 0x40000000ULL) return STO_ENOTSUP;
   }
   if (T > (1LL << 31) - 1) return STO_ENOTSUP;
@@ -911,6 +956,30 @@ int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
     hs[i]->inject_cta = -1;
     if (hs[i]->h_err[0] != 0) return hs[i]->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
   }
+  return STO_OK;
+}
+
+int sto_set_tableau(sto_handle* h, int32_t stages, const double* a, const double* b) {
+  if (!h) return STO_EINVAL;
+  if (stages == 0) {  // back to classic RK4
+    h->rk_stages = 4;
+    h->rk_classic = true;
+    return STO_OK;
+  }
+  if (stages < 1 || stages > 4 || !a || !b) return STO_EINVAL;
+  for (int i = 0; i < stages; ++i) {
+    if (!std::isfinite(b[i])) return STO_EINVAL;
+    for (int j = 0; j < stages; ++j) {
+      const double v = a[i * stages + j];
+      if (!std::isfinite(v) || (j >= i && v != 0.0)) return STO_EINVAL;  // explicit only
+    }
+  }
+  h->rk_stages = stages;
+  for (int i = 0; i < 4; ++i) {
+    h->rk_b[i] = i < stages ? b[i] : 0.0;
+    for (int j = 0; j < 4; ++j) h->rk_a[i * 4 + j] = (i < stages && j < stages) ? a[i * stages + j] : 0.0;
+  }
+  h->rk_classic = false;
   return STO_OK;
 }
 
@@ -989,6 +1058,7 @@ int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const f
   a.tag_base = 1u;
   a.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
   a.l2_keep = l2_keeps(N);
+  a.rk_stages = 4;
   set_constants(P, &a);
   STO_CUDA(launch_stepper_rowmajor(plan, a, s));
   int h_err[4] = {0, 0, 0, 0};
@@ -1016,7 +1086,7 @@ struct sto_batch {
   float* win = nullptr;
   float2* st = nullptr;       // mn | ms | ksum, each [3][R][N]
   sto::df* hs0 = nullptr;     // [R]
-  double* aing = nullptr;     // [R]
+  sto::df* aing = nullptr;    // [R] g A_in as double-float
   int* t_dev = nullptr;
   int* d_err = nullptr;
   int* h_err = nullptr;
@@ -1141,7 +1211,7 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
       !alloc(reinterpret_cast<void**>(&b->win), static_cast<size_t>(N) * n_in * 4) ||
       !alloc(reinterpret_cast<void**>(&b->st), 9 * RN * sizeof(float2)) ||
       !alloc(reinterpret_cast<void**>(&b->hs0), R * sizeof(sto::df)) ||
-      !alloc(reinterpret_cast<void**>(&b->aing), R * sizeof(double)) ||
+      !alloc(reinterpret_cast<void**>(&b->aing), R * sizeof(sto::df)) ||
       !alloc(reinterpret_cast<void**>(&b->t_dev), 16) ||
       !alloc(reinterpret_cast<void**>(&b->d_err), 16))
     return fail(STO_ENOMEM);
@@ -1185,7 +1255,7 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
   if (rc) return fail(rc);
   // per-reservoir constants
   std::vector<sto::df> hs0(R);
-  std::vector<double> aing(R);
+  std::vector<sto::df> aing(R);
   const double hs0_per_amp = params->hbar * params->eta * 1.0e7 /
                              (2.0 * params->e_charge * params->Ms * params->volume);
   for (int r = 0; r < R; ++r) {
@@ -1193,10 +1263,10 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
     const double gn = input_gain ? input_gain[r] : params->input_gain;
     if (!std::isfinite(I) || !std::isfinite(gn)) return fail(STO_EINVAL);
     hs0[r] = sto::df_split_host(hs0_per_amp * I);
-    aing[r] = params->A_in * gn;
+    aing[r] = sto::df_split_host(params->A_in * gn);
   }
   if ((e = cudaMemcpyAsync(b->hs0, hs0.data(), R * sizeof(sto::df), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(b->aing, aing.data(), R * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      (e = cudaMemcpyAsync(b->aing, aing.data(), R * sizeof(sto::df), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return fail(cuda_fail(e));
   // states: mn = ms = m0, ksum = 0  (device layout [3][R][N] df)
   std::vector<float2> st(9 * RN, make_float2(0.f, 0.f));

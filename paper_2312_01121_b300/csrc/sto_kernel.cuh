@@ -74,7 +74,13 @@ struct KArgs {
   double* g_acp;             // N partial sums of dL/dA_cp
   double* g_cur;             // N partial sums of dL/dI
   float dhs0_di_f;           // dH_s0/dI (the adjoint's dL/dI term)
+  // explicit Runge-Kutta tableau (TableauProgram; classic RK4 otherwise)
+  int rk_stages;             // stages per step (4 for classic RK4)
+  df rk_a[4][4];             // a[i][j], j < i
+  df rk_b[4];                // weights
 };
+
+enum ProgramKind { kProgForward = 0, kProgAdjoint = 1, kProgTableau = 2 };
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -378,6 +384,85 @@ struct ForwardProgram {
   }
 };
 
+// Any explicit Runge-Kutta method with up to four stages (Butcher tableau
+// a strictly lower triangular, weights b): with increments d_i = dt f(y_i),
+//   y_1 = m_n,  y_{i+1} = m_n + sum_{j<=i} a[i+1][j] d_j,  m_{n+1} = m_n + sum b_i d_i.
+// The paper closes by noting that its approach carries over to any
+// reservoir evolved by an explicit method; the engine is the same, only
+// the per-oscillator combination differs.
+struct TableauProgram {
+  df mn[3], ms[3], d0[3], d1[3], d2[3], acc[3], fa[3], fb[3], hin;
+  int t, sub, st;
+
+  __device__ __forceinline__ void load_hin(const KArgs& a, int node) {
+    double s = 0.0;
+    for (int jj = 0; jj < a.n_in; ++jj)
+      s += static_cast<double>(a.w_in[static_cast<size_t>(node) * a.n_in + jj]) *
+           static_cast<double>(a.u[static_cast<size_t>(t) * a.n_in + jj]);
+    hin = df_from_double(a.ain_g * s);
+  }
+
+  __device__ __forceinline__ void init(const KArgs& a, int node, const Publisher& pub, unsigned tag) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      mn[i] = df_from_double(a.state[static_cast<size_t>(i) * a.N + node]);
+      ms[i] = mn[i];
+    }
+    t = sub = st = 0;
+    load_hin(a, node);
+    pub(node, ms[0].hi, tag);
+    llg_affine(a, ms, fa, fb);
+  }
+
+  __device__ __forceinline__ void stage(const KArgs& a, int node, long long /*g*/, float hraw,
+                                        const Publisher& pub, unsigned next_tag) {
+    const df hx = df_add(df_mul_f(a.acp, hraw), hin);
+    df d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      d[i] = df_add(fa[i], df_mul(hx, fb[i]));
+      const df bd = df_mul(a.rk_b[st], d[i]);
+      acc[i] = st == 0 ? bd : df_add(acc[i], bd);
+    }
+    if (st + 1 < a.rk_stages) {
+      const int nx = st + 1;  // next stage: y = m_n + sum_{j<nx} a[nx][j] d_j
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (st == 0) d0[i] = d[i];
+        else if (st == 1) d1[i] = d[i];
+        else d2[i] = d[i];
+        df y = df_add(mn[i], df_mul(a.rk_a[nx][0], d0[i]));
+        if (nx > 1) y = df_add(y, df_mul(a.rk_a[nx][1], d1[i]));
+        if (nx > 2) y = df_add(y, df_mul(a.rk_a[nx][2], d2[i]));
+        ms[i] = y;
+      }
+      st = nx;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        mn[i] = df_add(mn[i], acc[i]);
+        ms[i] = mn[i];
+      }
+      st = 0;
+      if (++sub == a.S) {  // end of input sample t: sample the state
+        sub = 0;
+        if (a.states_out) {
+          const df v = a.comp == 0 ? mn[0] : (a.comp == 1 ? mn[1] : mn[2]);
+          a.states_out[static_cast<size_t>(t) * a.N + node] = v.hi;
+        }
+        if (++t < a.T) load_hin(a, node);
+      }
+    }
+    pub(node, ms[0].hi, next_tag);
+    llg_affine(a, ms, fa, fb);
+  }
+
+  __device__ __forceinline__ void finish(const KArgs& a, int node) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.state[static_cast<size_t>(i) * a.N + node] = df_to_double(mn[i]);
+  }
+};
+
 // Discrete adjoint of the RK4 step, run backwards over a recorded segment.
 // For step m' = m + dt/6 (k1 + 2 k2 + 2 k3 + k4), k_s = f(y_s), and the
 // cotangent lam = dL/dm':
@@ -580,7 +665,7 @@ struct AdjointProgram {
 // per panel).  kRowMajorW = true: a.W is the caller's row-major N x N matrix
 // (N a multiple of 4); each panel arrives as one bulk copy per row, issued by
 // the 32 lanes of the producer warp.  Consumers are identical in both.
-template <int RPW, bool kRowMajorW, bool kAdjoint = false>
+template <int RPW, bool kRowMajorW, int kProg = kProgForward>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int c = blockIdx.x;
@@ -624,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
     if (warp == kConsWarps) {
       const uint64_t pol = (a.resident || a.l2_keep) ? policy_evict_last() : policy_evict_first();
       const long long total =
-          a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
+          a.resident ? a.P : static_cast<long long>(a.P) * a.rk_stages * a.S * a.T;
       const float* Wrows = a.W + static_cast<size_t>(r0) * a.N;
       long long it = 0;
       int slot = 0, j = 0;
@@ -680,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
       const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
       const bool all_keep = a.resident || a.l2_keep;
       const long long total =
-          a.resident ? a.P : static_cast<long long>(a.P) * 4LL * a.S * a.T;
+          a.resident ? a.P : static_cast<long long>(a.P) * a.rk_stages * a.S * a.T;
       long long it = 0;
       int slot = 0, j = 0;
       uint32_t lap = 0;  // it / ns
@@ -728,7 +813,9 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   // owners sit in the first warps; the others gather while owners work
   const int owner_warps = (R_max + 31) / 32;
   const int gather_first = owner_warps < kConsWarps ? owner_warps * 32 : 0;
-  using Program = typename std::conditional<kAdjoint, AdjointProgram, ForwardProgram>::type;
+  using Program = typename std::conditional<
+      kProg == kProgAdjoint, AdjointProgram,
+      typename std::conditional<kProg == kProgTableau, TableauProgram, ForwardProgram>::type>::type;
   Program prog;
   unsigned tag = a.tag_base;
   if (owner) prog.init(a, node, pub, tag);
@@ -748,7 +835,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
     }
     aborted = consumer_sync_or(!landed);
   }
-  const long long n_stages = 4LL * a.S * a.T;
+  const long long n_stages = static_cast<long long>(a.rk_stages) * a.S * a.T;
   for (long long g = 0; g < n_stages && !aborted; ++g) {
     // 1. the stage's published value of every oscillator
     bool fail = false;

@@ -225,7 +225,7 @@ struct EpiArgs {
   __nv_bfloat16* Xs;        // Xt tiles
   float* states_out;        // [T][R][N] or nullptr
   const df* hs0_r;          // per reservoir H_s0
-  const double* ain_g_r;    // per reservoir g A_in
+  const df* ain_g_r;        // per reservoir g A_in
   int N, R, Kpad, n_in, comp, st, last_sub;
   KArgs c;                  // shared constants (gdt, alpha, happl, hkp, lambda, p, acp, sixth)
 };
@@ -256,9 +256,10 @@ __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df
 // m_n and writes (sum, stage state); stages 1-2 update both; stage 3 writes
 // m_{n+1} only (the next stage 0 starts from it).
 __global__ void __launch_bounds__(256) sweep_epilogue_kernel(const __grid_constant__ EpiArgs e) {
-  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (idx >= static_cast<long long>(e.R) * e.N) return;
-  const int r = static_cast<int>(idx / e.N), k = static_cast<int>(idx % e.N);
+  // R N <= 2^31 (checked at create): 32-bit index arithmetic
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<unsigned>(e.R) * static_cast<unsigned>(e.N)) return;
+  const unsigned r = idx / static_cast<unsigned>(e.N), k = idx - r * static_cast<unsigned>(e.N);
   const size_t RN = static_cast<size_t>(e.R) * e.N;
   const int t = *e.t_dev;
   const int st = e.st;
@@ -275,11 +276,13 @@ __global__ void __launch_bounds__(256) sweep_epilogue_kernel(const __grid_consta
       ms[i] = mn[i];
     }
   }
-  double s = 0.0;
-  for (int j = 0; j < e.n_in; ++j)
-    s += static_cast<double>(e.w_in[static_cast<size_t>(k) * e.n_in + j]) *
-         static_cast<double>(e.u[static_cast<size_t>(t) * e.n_in + j]);
-  const df hx = df_add(df_mul_f(e.c.acp, e.Dt[idx]), df_from_double(e.ain_g_r[r] * s));
+  // input drive w_in . u_t in double-float (each product exact), no FP64:
+  // that pipe runs at 1/64 of the FP32 rate here
+  df s = two_prod(e.w_in[static_cast<size_t>(k) * e.n_in], e.u[static_cast<size_t>(t) * e.n_in]);
+  for (int j = 1; j < e.n_in; ++j)
+    s = df_add(s, two_prod(e.w_in[static_cast<size_t>(k) * e.n_in + j],
+                           e.u[static_cast<size_t>(t) * e.n_in + j]));
+  const df hx = df_add(df_mul_f(e.c.acp, e.Dt[idx]), df_mul(e.ain_g_r[r], s));
   df d[3];
   sweep_increment(e.c, e.hs0_r[r], ms, hx, d);
 #pragma unroll

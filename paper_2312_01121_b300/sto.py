@@ -92,6 +92,7 @@ SIGNATURES = {
     "sto_batch_get_state": (ctypes.c_int, [_VP, _VP]),
     "sto_batch_destroy": (None, [_VP]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
+    "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
 }
 
 _lib = None
@@ -350,6 +351,15 @@ class Reservoir:
         if want_m0:
             g["m0"] = dm
         return g
+
+    def set_tableau(self, a=None, b=None):
+        """Explicit Runge-Kutta tableau (a: s x s strictly lower, b: s); None = RK4."""
+        if b is None:
+            _check(load_library().sto_set_tableau(self.handle, 0, None, None))
+            return
+        A = np.ascontiguousarray(a, dtype=np.float64)
+        B = np.ascontiguousarray(b, dtype=np.float64)
+        _check(load_library().sto_set_tableau(self.handle, len(B), A.ctypes.data, B.ctypes.data))
 
     def set_input_weights(self, w_in):
         sto_set_input_weights(self.handle, w_in)
