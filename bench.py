@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--sweep-n", type=int, default=2500)
     ap.add_argument("--sweep-r", type=int, default=512)
     ap.add_argument("--sweep-t", type=int, default=2, help="input samples per timed sweep call")
+    ap.add_argument("--sweep-plan", default="", help="tile_n,slots of the sweep kernel (default: autotuned)")
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
@@ -329,9 +330,11 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
     P = sto.Params(substeps=args.substeps)
     sw = sto.Sweep(torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), P, currents=cur,
                    gains=gain, m0=torch.from_numpy(m0).to(dev), stream=torch.cuda.current_stream())
+    if args.sweep_plan:
+        sw.set_plan(*(int(x) for x in args.sweep_plan.split(",")))
     u_d = torch.from_numpy(u).to(dev)
     st = torch.empty((T, R, N), dtype=torch.float32, device=dev)
-    sw.run(u_d[:T], st)  # warm-up: graph capture path, caches
+    sw.run(u_d[:T], st)  # warm-up (and the autotuner, unless a plan was given)
     torch.cuda.synchronize()
     reps = 3
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,10 +346,12 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     finite = bool(torch.isfinite(st).all().item())
+    plan = sw.plan()
     sw.close()
     stages = 4 * args.substeps * T
     us_stage = ms * 1e3 / stages
-    Mpad, Kpad, Rpad = -(-N // 128) * 128, -(-N // 64) * 64, -(-R // 64) * 64
+    Mpad, Kpad = -(-N // 128) * 128, -(-N // 64) * 64
+    Rpad = -(-R // plan["tile_n"]) * plan["tile_n"]
     alg_flop = 2.0 * N * N * R            # the coupling product W X of one stage
     exe_flop = 2.0 * Mpad * (2 * Kpad) * Rpad  # executed: hi/lo split, padded tiles
     return {"workload": f"{R} reservoirs sharing one N={N} Gaussian W (BF16), I~U[1,3] mA, "
@@ -358,7 +363,8 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
             "tensor_peak_tflops": peaks.get("bf16"),
             "frac_of_bf16_peak_whole_stage": (exe_flop / (us_stage * 1e-6) / 1e12) / peaks["bf16"]
             if peaks.get("bf16") else None,
-            "finite": finite}
+            "finite": finite, "plan": plan,
+            "launches_per_call": 1}
 
 
 def time_group(args, seed, torch, sto, dev, hbm_peak):

@@ -267,11 +267,42 @@ STO_API int sto_batch_create(int64_t N, int32_t R, const sto_params* params,
 
 /* Advance every reservoir over T input samples of the shared series u
  * (T x n_in, host or device).  states_out: T x R x N float32 (sample,
- * reservoir, oscillator; host or device) or NULL.  One input sample is
- * captured as a CUDA graph (substeps x 4 pairs of product and torque
- * kernels) and replayed T times.
- * Errors: STO_EINVAL, STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA. */
+ * reservoir, oscillator; host or device) or NULL.  The call is one
+ * persistent cooperative launch (captured with its barrier reset as a CUDA
+ * graph): per RK4 stage every CTA multiplies its tiles of D = W X on the
+ * tensor cores and finishes them (torque, RK4 combination, next X), then
+ * all CTAs meet at a grid barrier.  The first call without a plan runs the
+ * autotuner (sto_batch_set_plan(b, 0, 0)).  4 * substeps * T <= 2^30.
+ * Errors: STO_EINVAL, STO_ENOMEM, STO_ENOTSUP, STO_ETIMEOUT, STO_ECUDA. */
 STO_API int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out);
+
+/* Launch plan of the sweep kernel. */
+typedef struct {
+  int32_t tile_n;              /* reservoirs per tile (BN): MMA N = 2 BN (hi and lo terms), multiple of 16 */
+  int32_t slots;               /* depth of the shared-memory copy ring */
+  int32_t grid;                /* CTAs of the persistent launch */
+  int32_t tiles;               /* 128-oscillator x BN-reservoir tiles per stage */
+  int32_t smem_bytes;          /* dynamic shared memory per CTA */
+  int32_t tuned;               /* 1: chosen by timing candidates; 0: set by the caller or none yet */
+  int32_t candidates;          /* candidates the autotuner timed */
+  float tuned_us_per_stage;    /* the winner's time per stage in the tuning run */
+  int32_t staged;              /* 1: the epilogue copies the next pair's state to shared memory ahead */
+  int32_t reserved[3];
+} sto_batch_plan;
+
+/* Set the plan: tile_n (multiple of 16 in [16, 128]) and slots (3, 6 or 9:
+ * three copy warps own every third slot; the state staging buffer is used
+ * when it fits beside the ring), or (0, 0) to time every candidate (tile_n
+ * in {16, 32, ..., 128} up to R, slots in {3, 6}, staging on and off) on two
+ * RK4 steps of zero input from the batch's state
+ * (restored afterwards) and keep the fastest.  Tuned plans are cached per
+ * (device, N, R) for the life of the process.  The stage state is kept.
+ * Errors: STO_EINVAL, STO_ENOTSUP (plan cannot run: shared memory, tile
+ * shape), STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA.  No counterpart in the paper. */
+STO_API int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots);
+
+/* The current plan (all zero before the first run or set_plan). */
+STO_API int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out);
 
 /* FP64 states, R x 3 x N (host or device). */
 STO_API int sto_batch_get_state(const sto_batch* b, double* m);

@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -30,6 +32,9 @@ int cuda_fail(cudaError_t e) {
   g_last_cuda = e;
   return STO_ECUDA;
 }
+
+// STO_OK, or STO_ECUDA with the error recorded.
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STO_OK : cuda_fail(e); }
 
 #define STO_CUDA(call)                         \
   do {                                         \
@@ -218,13 +223,27 @@ int smem_optin_limit() {
   return cached[dev];
 }
 
+// Raise a kernel's dynamic shared-memory cap to what the device allows next
+// to its static shared memory; the room left, or -1.
+template <typename F>
+int raise_dyn_smem_cap(F* func) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const int room = smem_optin_limit() - static_cast<int>(fa.sharedSizeBytes);
+  if (room <= 0 || cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return room;
+}
+
 template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  const int cap = smem_optin_limit();
-  if (cap < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  if (e != cudaSuccess) return e;
+  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>);
+  if (room < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.G);
   cfg.blockDim = dim3(sto::kThreads);
@@ -1070,7 +1089,14 @@ int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const f
 
 // ---------------------------------------------------------------- sweep
 
-}  // extern "C"
+// Launch plan of the persistent sweep kernel: tile width (reservoirs per
+// tile), copy-ring depth, CTAs.
+struct SweepPlan {
+  int bn = 0, slots = 0, G = 0, tiles_m = 0, tiles_n = 0, acc_cols = 0, staged = 0;
+  size_t smem = 0;
+};
+
+}  // namespace
 
 struct sto_batch {
   cudaStream_t stream = nullptr;      // the caller's stream
@@ -1078,22 +1104,26 @@ struct sto_batch {
   cudaEvent_t ev = nullptr;
   int64_t N = 0;
   int32_t R = 0;
-  int Mpad = 0, Kpad = 0, Rpad = 0;
+  int Mpad = 0, Kpad = 0;
   sto_params params{};
   __nv_bfloat16* Wb = nullptr;
-  __nv_bfloat16* Xs = nullptr;
-  float* Dt = nullptr;
+  __nv_bfloat16* X[2] = {nullptr, nullptr};  // stage operands in the plan's tile layout
+  size_t x_cap = 0;                   // BF16 values per X buffer
   float* win = nullptr;
   float2* st = nullptr;       // mn | ms | ksum, each [3][R][N]
   sto::df* hs0 = nullptr;     // [R]
   sto::df* aing = nullptr;    // [R] g A_in as double-float
-  int* t_dev = nullptr;
+  unsigned long long* gbar = nullptr;  // grid barrier counter
   int* d_err = nullptr;
   int* h_err = nullptr;
   float* d_u = nullptr;
   size_t d_u_cap = 0;
   float* d_states = nullptr;
   size_t d_states_cap = 0;
+  SweepPlan plan;
+  bool planned = false;
+  int tuned = 0, candidates = 0;
+  float tuned_us = 0.f;
 };
 
 namespace {
@@ -1101,13 +1131,13 @@ namespace {
 void free_batch(sto_batch* b) {
   if (!b) return;
   cudaFree(b->Wb);
-  cudaFree(b->Xs);
-  cudaFree(b->Dt);
+  cudaFree(b->X[0]);
+  cudaFree(b->X[1]);
   cudaFree(b->win);
   cudaFree(b->st);
   cudaFree(b->hs0);
   cudaFree(b->aing);
-  cudaFree(b->t_dev);
+  cudaFree(b->gbar);
   cudaFree(b->d_err);
   cudaFree(b->d_u);
   cudaFree(b->d_states);
@@ -1117,53 +1147,253 @@ void free_batch(sto_batch* b) {
   delete b;
 }
 
-// Enqueue one input sample of the sweep: S RK4 steps of four
-// (tensor-core product, epilogue) pairs, then advance the sample counter.
-int batch_enqueue_sample(sto_batch* b, const float* d_u, float* d_states) {
-  const sto_params& P = b->params;
+// Plan for tile width bn and ring depth slots, or false when it cannot run:
+// bn a multiple of 16 in [16, 256] (tcgen05 M = 128 shapes), shared memory
+// within the device limit, every CTA resident (one per SM).
+bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, SweepPlan* out) {
+  if (bn < 16 || bn > 128 || bn % 16 != 0 || slots < sto::kSpProducers || slots > sto::kSpMaxSlots ||
+      slots % sto::kSpProducers != 0)
+    return false;
+  SweepPlan p;
+  p.bn = bn;
+  p.slots = slots;
+  p.tiles_m = b->Mpad / sto::kSwM;
+  p.tiles_n = (b->R + bn - 1) / bn;
+  p.acc_cols = 2 * bn <= 32 ? 32 : (2 * bn <= 64 ? 64 : (2 * bn <= 128 ? 128 : 256));  // [hi | lo] columns
+  p.staged = staged ? 1 : 0;
+  p.smem = static_cast<size_t>(slots) * (sto::kSwSliceA + 2u * bn * sto::kSwK * 2u) +
+           (staged ? sto::kSpStageAll : 0) + sto::kSpAlignSlack;
+  const int room = raise_dyn_smem_cap(sto::sweep_persistent_kernel);
+  if (room < 0 || p.smem > static_cast<size_t>(room)) return false;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sto::sweep_persistent_kernel, sto::kSpThreads,
+                                                    p.smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  // balanced grid: the fewest CTAs that keep the most loaded one at the
+  // minimum number of tiles
+  const long long n_tiles = static_cast<long long>(p.tiles_m) * p.tiles_n;
+  const long long slots_avail = static_cast<long long>(sms) * 1;  // one CTA per SM (928 threads)
+  const long long per = (n_tiles + slots_avail - 1) / slots_avail;
+  p.G = static_cast<int>((n_tiles + per - 1) / per);
+  *out = p;
+  return true;
+}
+
+// Make X buffers for the plan and publish the current stage state into X[0].
+int sweep_apply_plan(sto_batch* b, const SweepPlan& p) {
   cudaStream_t s = b->own;
-  sto::GemmArgs g{};
-  g.Wb = b->Wb;
-  g.Xs = b->Xs;
-  g.Dt = b->Dt;
-  g.err = b->d_err;
-  g.N = static_cast<int>(b->N);
-  g.R = b->R;
-  g.Kpad = b->Kpad;
-  g.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
-  sto::EpiArgs e{};
-  e.Dt = b->Dt;
-  e.w_in = b->win;
-  e.u = d_u;
-  e.t_dev = b->t_dev;
+  const size_t need = static_cast<size_t>(p.tiles_n) * p.bn * 2 * b->Kpad;
+  if (need > b->x_cap) {
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(b->X[i]);
+      b->X[i] = nullptr;
+      if (cudaMalloc(reinterpret_cast<void**>(&b->X[i]), need * 2) != cudaSuccess) {
+        cudaGetLastError();
+        b->x_cap = 0;
+        return STO_ENOMEM;
+      }
+    }
+    b->x_cap = need;
+  }
   const size_t RN = static_cast<size_t>(b->R) * b->N;
-  e.mn = b->st;
-  e.ms = b->st + 3 * RN;
-  e.ksum = b->st + 6 * RN;
-  e.Xs = b->Xs;
-  e.states_out = d_states;
-  e.hs0_r = b->hs0;
-  e.ain_g_r = b->aing;
-  e.N = static_cast<int>(b->N);
-  e.R = b->R;
-  e.Kpad = b->Kpad;
-  e.n_in = P.n_in;
-  e.comp = P.sample_component;
-  set_constants(P, &e.c);
-  const dim3 ggrid(b->Mpad / sto::kSwM, b->Rpad / sto::kSwN);
-  const unsigned eblocks = static_cast<unsigned>((RN + 255) / 256);
-  for (int sub = 0; sub < P.substeps; ++sub) {
-    for (int st = 0; st < 4; ++st) {
-      sto::sweep_gemm_kernel<<<ggrid, sto::kSwThreads, sto::kSwSmem, s>>>(g);
-      STO_CUDA(cudaGetLastError());
-      e.st = st;
-      e.last_sub = sub == P.substeps - 1;
-      sto::sweep_epilogue_kernel<<<eblocks, 256, 0, s>>>(e);
-      STO_CUDA(cudaGetLastError());
+  STO_CUDA(cudaMemsetAsync(b->X[0], 0, need * 2, s));
+  STO_CUDA(cudaMemsetAsync(b->X[1], 0, need * 2, s));
+  sto::sweep_publish_kernel<<<static_cast<unsigned>((RN + 255) / 256), 256, 0, s>>>(
+      b->st + 3 * RN, b->X[0], static_cast<int>(b->N), b->R, b->Kpad, p.bn);
+  STO_CUDA(cudaGetLastError());
+  b->plan = p;
+  b->planned = true;
+  return STO_OK;
+}
+
+// Enqueue one persistent launch over T input samples on the sweep's stream.
+int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float* d_states) {
+  const sto_params& P = b->params;
+  const SweepPlan& p = b->plan;
+  cudaStream_t s = b->own;
+  sto::SweepArgs a{};
+  const size_t RN = static_cast<size_t>(b->R) * b->N;
+  a.Wb = b->Wb;
+  a.X0 = b->X[0];
+  a.X1 = b->X[1];
+  a.mn = b->st;
+  a.ms = b->st + 3 * RN;
+  a.ksum = b->st + 6 * RN;
+  a.states_out = d_states;
+  a.w_in = b->win;
+  a.u = d_u;
+  a.hs0_r = b->hs0;
+  a.ain_g_r = b->aing;
+  a.err = b->d_err;
+  a.gbar = b->gbar;
+  a.N = static_cast<int>(b->N);
+  a.R = b->R;
+  a.Kpad = b->Kpad;
+  a.n_in = P.n_in;
+  a.comp = P.sample_component;
+  a.S = substeps;
+  a.T = static_cast<int>(T);
+  a.bn = p.bn;
+  a.slots = p.slots;
+  a.tiles_m = p.tiles_m;
+  a.tiles_n = p.tiles_n;
+  a.acc_cols = p.acc_cols;
+  a.staged = p.staged;
+  a.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
+  set_constants(P, &a.c);
+  STO_CUDA(cudaMemsetAsync(b->gbar, 0, 8, s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.G);
+  cfg.blockDim = dim3(sto::kSpThreads);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: they meet at the grid barrier
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  STO_CUDA(cudaLaunchKernelEx(&cfg, sto::sweep_persistent_kernel, a));
+  return STO_OK;
+}
+
+// Tile widths and ring depths the autotuner times.
+constexpr int kTuneBn[] = {16, 32, 48, 64, 80, 96, 112, 128};
+constexpr int kTuneSlots[] = {3, 6};
+
+struct TuneKey {
+  int dev;
+  int64_t N;
+  int32_t R;
+  bool operator<(const TuneKey& o) const {
+    return dev != o.dev ? dev < o.dev : (N != o.N ? N < o.N : R < o.R);
+  }
+};
+
+// Process-wide cache of tuned plans (bn, slots, measured us per stage).
+std::map<TuneKey, std::array<float, 3>>& tune_cache() {
+  static std::map<TuneKey, std::array<float, 3>> m;
+  return m;
+}
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+// Time every valid (bn, slots) on a short run (2 RK4 steps of one sample of
+// zero input) from the batch's own state, restore the state, keep the
+// fastest.  Results are cached per (device, N, R) for the process.
+int sweep_autotune(sto_batch* b) {
+  int dev = 0;
+  STO_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{dev, b->N, b->R};
+  {
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      SweepPlan p;
+      const int code = static_cast<int>(it->second[1]);
+      if (sweep_plan(b, static_cast<int>(it->second[0]), code / 2, code % 2, &p)) {
+        const int rc = sweep_apply_plan(b, p);
+        if (rc) return rc;
+        b->tuned = 1;
+        b->tuned_us = it->second[2];
+        return STO_OK;
+      }
     }
   }
-  sto::sweep_advance_kernel<<<1, 1, 0, s>>>(b->t_dev);
-  STO_CUDA(cudaGetLastError());
+  cudaStream_t s = b->own;
+  const size_t RN = static_cast<size_t>(b->R) * b->N;
+  float2* saved = nullptr;
+  float* u0 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(saved);
+    cudaFree(u0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(reinterpret_cast<void**>(&saved), 9 * RN * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&u0), 64 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return STO_ENOMEM;
+  }
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+      (e = cudaMemsetAsync(u0, 0, 64 * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(saved, b->st, 9 * RN * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e);
+  }
+  float best = 0.f;
+  SweepPlan best_p;
+  int n = 0;
+  int rc = STO_OK;
+  for (int bn : kTuneBn) {
+    if (bn > ((b->R + 15) / 16) * 16) break;  // tiles wider than R only add padding
+    for (int cand = 0; cand < 2 * static_cast<int>(sizeof(kTuneSlots) / sizeof(kTuneSlots[0])); ++cand) {
+      const int slots = kTuneSlots[cand / 2], staged = cand % 2;
+      SweepPlan p;
+      if (!sweep_plan(b, bn, slots, staged, &p)) continue;
+      if ((rc = sweep_apply_plan(b, p)) != STO_OK) break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && rc == STO_OK; ++rep) {
+        if ((e = cudaMemsetAsync(b->d_err, 0, 16, s)) != cudaSuccess || (e = cudaEventRecord(e0, s)) != cudaSuccess) {
+          rc = cuda_fail(e);
+          break;
+        }
+        if ((rc = sweep_enqueue(b, u0, 1, 2, nullptr)) != STO_OK) break;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(b->h_err, b->d_err, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+          rc = cuda_fail(e);
+          break;
+        }
+        if (b->h_err[0] != 0) {
+          rc = b->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+          break;
+        }
+      }
+      if (rc) break;
+      const float us = ms * 1000.f / 8.f;  // the last of three runs, per stage
+      ++n;
+      if (n == 1 || us < best) {
+        best = us;
+        best_p = p;
+      }
+      // back to the state before the trial
+      if ((e = cudaMemcpyAsync(b->st, saved, 9 * RN * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        rc = cuda_fail(e);
+        break;
+      }
+    }
+    if (rc) break;
+  }
+  if (rc == STO_OK && n == 0) rc = STO_ENOTSUP;
+  if (rc == STO_OK) {
+    rc = cuda_rc(cudaMemcpyAsync(b->st, saved, 9 * RN * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (rc == STO_OK) rc = sweep_apply_plan(b, best_p);
+    if (rc == STO_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+  } else {
+    cudaMemcpyAsync(b->st, saved, 9 * RN * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    b->planned = false;
+  }
+  cleanup();
+  if (rc) return rc;
+  b->tuned = 1;
+  b->candidates = n;
+  b->tuned_us = best;
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  tune_cache()[key] = {static_cast<float>(best_p.bn), static_cast<float>(best_p.slots * 2 + best_p.staged), best};
   return STO_OK;
 }
 
@@ -1188,7 +1418,6 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
   b->params = *params;
   b->Mpad = static_cast<int>((N + sto::kSwM - 1) / sto::kSwM * sto::kSwM);
   b->Kpad = static_cast<int>((N + sto::kSwK - 1) / sto::kSwK * sto::kSwK);
-  b->Rpad = (R + sto::kSwN - 1) / sto::kSwN * sto::kSwN;
   cudaStream_t s = b->stream;
   auto fail = [&](int code) {
     if (b->stream) cudaStreamSynchronize(b->stream);
@@ -1206,13 +1435,11 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
     return true;
   };
   if (!alloc(reinterpret_cast<void**>(&b->Wb), static_cast<size_t>(b->Mpad) * b->Kpad * 2) ||
-      !alloc(reinterpret_cast<void**>(&b->Xs), static_cast<size_t>(b->Rpad) * 2 * b->Kpad * 2) ||
-      !alloc(reinterpret_cast<void**>(&b->Dt), RN * 4) ||
       !alloc(reinterpret_cast<void**>(&b->win), static_cast<size_t>(N) * n_in * 4) ||
       !alloc(reinterpret_cast<void**>(&b->st), 9 * RN * sizeof(float2)) ||
       !alloc(reinterpret_cast<void**>(&b->hs0), R * sizeof(sto::df)) ||
       !alloc(reinterpret_cast<void**>(&b->aing), R * sizeof(sto::df)) ||
-      !alloc(reinterpret_cast<void**>(&b->t_dev), 16) ||
+      !alloc(reinterpret_cast<void**>(&b->gbar), 16) ||
       !alloc(reinterpret_cast<void**>(&b->d_err), 16))
     return fail(STO_ENOMEM);
   if (cudaMallocHost(reinterpret_cast<void**>(&b->h_err), 16) != cudaSuccess) {
@@ -1287,16 +1514,42 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
         st[3 * RN + i * RN + static_cast<size_t>(r) * N + k] = make_float2(d.hi, d.lo);
       }
   if ((e = cudaMemcpyAsync(b->st, st.data(), st.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b->Xs, 0, static_cast<size_t>(b->Rpad) * 2 * b->Kpad * 2, s)) != cudaSuccess)
-    return fail(cuda_fail(e));
-  sto::sweep_publish_kernel<<<static_cast<unsigned>((RN + 255) / 256), 256, 0, s>>>(
-      b->st + 3 * RN, b->Xs, static_cast<int>(N), R, b->Kpad);
-  if ((e = cudaGetLastError()) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sto::sweep_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                sto::kSwSmem)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(cuda_fail(e));
+  // the launch plan (tile width, ring depth) is chosen by the first run
+  // (autotuner) or by sto_batch_set_plan
   *out = b;
+  return STO_OK;
+}
+
+int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots) {
+  if (!b) return STO_EINVAL;
+  cudaStreamSynchronize(b->stream);
+  if (tile_n == 0 && slots == 0) return sweep_autotune(b);
+  SweepPlan p;
+  // stage the epilogue's state through shared memory when it fits beside the ring
+  if (!sweep_plan(b, tile_n, slots, 1, &p) && !sweep_plan(b, tile_n, slots, 0, &p)) return STO_ENOTSUP;
+  int rc = sweep_apply_plan(b, p);
+  if (rc) return rc;
+  b->tuned = 0;
+  b->candidates = 0;
+  b->tuned_us = 0.f;
+  return cuda_rc(cudaStreamSynchronize(b->own));
+}
+
+int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out) {
+  if (!b || !out) return STO_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  if (!b->planned) return STO_OK;
+  out->tile_n = b->plan.bn;
+  out->slots = b->plan.slots;
+  out->grid = b->plan.G;
+  out->tiles = b->plan.tiles_m * b->plan.tiles_n;
+  out->smem_bytes = static_cast<int32_t>(b->plan.smem);
+  out->tuned = b->tuned;
+  out->candidates = b->candidates;
+  out->tuned_us_per_stage = b->tuned_us;
+  out->staged = b->plan.staged;
   return STO_OK;
 }
 
@@ -1305,7 +1558,14 @@ int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out) 
   if (T == 0) return STO_OK;
   if (!u) return STO_EINVAL;
   const sto_params& P = b->params;
+  if (T > (1LL << 31) - 1 || 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T) > 0x40000000ULL)
+    return STO_ENOTSUP;
   cudaStream_t s = b->stream;
+  if (!b->planned) {
+    cudaStreamSynchronize(s);
+    const int rc = sweep_autotune(b);
+    if (rc) return rc;
+  }
   const size_t n_u = static_cast<size_t>(T) * P.n_in;
   const size_t n_states = static_cast<size_t>(T) * b->R * b->N;
   int rc = grow(&b->d_u, &b->d_u_cap, n_u);
@@ -1318,16 +1578,15 @@ int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out) 
     if (rc) return rc;
     d_states = b->d_states;
   }
-  STO_CUDA(cudaMemsetAsync(b->t_dev, 0, 4, s));
   STO_CUDA(cudaMemsetAsync(b->d_err, 0, 16, s));
   // the sweep runs on its own stream, ordered after the caller's work
   STO_CUDA(cudaEventRecord(b->ev, s));
   STO_CUDA(cudaStreamWaitEvent(b->own, b->ev, 0));
-  // one input sample as a CUDA graph, replayed T times
+  // the call (barrier reset + one persistent launch) as a CUDA graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   STO_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
-  rc = batch_enqueue_sample(b, b->d_u, d_states);
+  rc = sweep_enqueue(b, b->d_u, T, P.substeps, d_states);
   const cudaError_t ce = cudaStreamEndCapture(b->own, &graph);
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
@@ -1335,9 +1594,7 @@ int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out) 
   }
   if (ce != cudaSuccess) return cuda_fail(ce);
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e == cudaSuccess) {
-    for (int64_t t = 0; t < T && e == cudaSuccess; ++t) e = cudaGraphLaunch(exec, b->own);
-  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->own);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->own);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, 16, cudaMemcpyDeviceToHost, s);

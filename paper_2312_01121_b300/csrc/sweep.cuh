@@ -6,23 +6,34 @@
 // (N x R), which runs on the 5th-generation tensor cores (tcgen05.mma,
 // BF16 operands, FP32 accumulation in tensor memory).  The stage value X is
 // split into two BF16 terms, X = X_hi + X_lo, and both are multiplied by the
-// BF16-rounded W in one K-concatenated product, so the only rounding the
-// product adds to FP32 accumulation is that of W itself.  The per-element
-// torque, RK4 combination and state (double-float, as in the single
-// reservoir stepper) run in a second kernel over all R x N pairs.
+// BF16-rounded W, so the only rounding the product adds to FP32 accumulation
+// is that of W itself.  The two terms are stacked along N (one MMA of width
+// 2 BN per K step reads each W slice once; the tensor cores are bound by
+// shared-memory bandwidth at these widths) and summed in the epilogue.
+//
+// One persistent cooperative launch runs a whole sto_run_batched call.  The
+// product is cut into tiles of 128 oscillators x BN reservoirs; CTA c takes
+// tiles c, c + G, ... of every stage.  Warp 0 streams the K slices of a tile
+// (one W slice and the matching X_hi and X_lo slices, 1-D bulk copies) through
+// a shared-memory ring and issues the MMAs into one of two tensor-memory
+// accumulators; the other 28 warps read the finished accumulator with
+// tcgen05.ld and run the per-pair epilogue (double-float torque, RK4
+// combination, BF16 split of the next X, sampling) while the next tile's MMAs
+// fill the other accumulator.  A stage ends with a grid barrier (every CTA's
+// X for the next stage written) before the next stage's first copy.
 //
 // Layouts.  Both product operands are kept in global memory in the order
 // the tensor cores read them from shared memory, so one K slice of one tile
-// is a single contiguous block fetched with one bulk copy (TMA):
+// is a single contiguous block:
 //   Wt   tile (i, j) = rows [128 i, 128 i + 128) x columns [64 j, 64 j + 64)
 //        of W (BF16, zero padded), 16 KB at ((i * Kpad/64) + j) * 16 KB;
-//   Xt   tile (n, j) = reservoirs [64 n, 64 n + 64) x columns [64 j, 64 j + 64)
-//        of [X_hi | X_lo] (K = 2 Kpad), 8 KB at ((n * 2Kpad/64) + j) * 8 KB;
-//   inside a tile: 8-row x 16-byte core matrices, column chunk c (8 values)
-//   at c * (rows/8) * 128 B, row group g at g * 128 B, row r % 8 at 16 B steps
-//   (the no-swizzle K-major layout: LBO = (rows/8) * 128 B, SBO = 128 B).
-//   Dt   [R][N] float (D transposed: reservoir-major)
-//   state: mn, ms, ksum as df pairs, [3][R][N] each
+//   Xt   tile (n, j) = reservoirs [BN n, BN n + BN) x columns [64 j, 64 j + 64)
+//        of [X_hi | X_lo] (K = 2 Kpad), BN * 128 B at ((n * 2Kpad/64) + j) * BN * 128 B;
+//   inside a tile: the 128-byte-swizzled K-major layout the tensor cores read
+//   at full shared-memory bandwidth: row r (64 K values = 128 B) at r * 128 B,
+//   its 16-byte chunk c (8 values) stored at chunk position c ^ (r % 8); 8-row
+//   groups are 1024 B apart (SBO), and slots start on 1024-byte boundaries.
+//   state: mn, ms, ksum as df pairs, [3][R][N] each.
 #pragma once
 
 #include <cstdint>
@@ -33,33 +44,49 @@
 
 namespace sto {
 
-constexpr int kSwM = 128;          // tile rows (oscillators)
-constexpr int kSwN = 64;           // tile columns (reservoirs)
-constexpr int kSwK = 64;           // K slice per pipeline stage
-constexpr int kSwSlots = 3;        // pipeline depth (96 KB: two CTAs per SM, one wave of tiles)
-constexpr int kSwThreads = 128;    // 4 warps: TMEM lanes 0..127
-constexpr int kSwSliceA = kSwM * kSwK * 2;        // 16 KB of W
-constexpr int kSwSliceB = kSwN * kSwK * 2;        // 8 KB of X_hi, 8 KB of X_lo
-constexpr int kSwSlot = kSwSliceA + 2 * kSwSliceB;
-constexpr int kSwSmem = kSwSlots * kSwSlot + 128;
+constexpr int kSwM = 128;          // tile rows (oscillators) = TMEM lanes
+constexpr int kSwK = 64;           // K slice per copy
+constexpr int kSwSliceA = kSwM * kSwK * 2;             // 16 KB of W per slice
+constexpr int kSpEpiPerQuarter = 7;                    // epilogue warps per TMEM lane quarter
+constexpr int kSpEpiWarps = 4 * kSpEpiPerQuarter;      // 28
+// Copies issued by one thread complete one after another (about 0.4 us
+// each, however many are in flight), so three warps issue them, each owning
+// every third ring slot.
+constexpr int kSpProducers = 3;
+constexpr int kSpEpiFirst = 1 + kSpProducers;          // warp 0 multiplies, 1..3 copy
+constexpr int kSpThreads = 32 * (kSpEpiFirst + kSpEpiWarps);  // 1024
+constexpr int kSpMaxSlots = 9;
 
-struct GemmArgs {
+struct SweepArgs {
   const __nv_bfloat16* Wb;   // Wt tiles
-  const __nv_bfloat16* Xs;   // Xt tiles
-  float* Dt;                 // [R][N]
+  __nv_bfloat16* X0;         // Xt tiles read by even stages (written by odd ones)
+  __nv_bfloat16* X1;         // Xt tiles read by odd stages
+  float2* mn;                // [3][R][N] df
+  float2* ms;
+  float2* ksum;
+  float* states_out;         // [T][R][N] or nullptr
+  const float* w_in;         // N x n_in (shared)
+  const float* u;            // T x n_in
+  const df* hs0_r;           // per reservoir H_s0
+  const df* ain_g_r;         // per reservoir g A_in
   int* err;                  // int32[4], as the stepper's
-  int N, R, Kpad;
+  unsigned long long* gbar;  // grid barrier counter, zero at launch
+  int N, R, Kpad, n_in, comp, S, T;
+  int bn, slots, tiles_m, tiles_n, acc_cols;  // plan: tile width, ring depth, tiles, TMEM columns per accumulator
+  int staged;                // 1: the next pair's state is copied to shared memory ahead (cp.async)
   unsigned long long timeout_ns;
+  KArgs c;                   // shared constants (gdt, alpha, happl, hkp, lambda, p, acp, sixth)
 };
 
 // Shared-memory matrix descriptor of tcgen05.mma for a K-major operand in the
-// no-swizzle layout: 8-row x 16-byte core matrices, `lbo` bytes between
-// core matrices adjacent in K, `sbo` bytes between core matrices adjacent in
-// rows; bits 46-47 hold the descriptor version (1).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
-         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
-         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// 128-byte swizzle layout: start address >> 4 (bits 0-13), the unused
+// leading-dimension offset (1), 1024 B between 8-row groups (bits 32-45),
+// descriptor version 1 (bits 46-47), layout type 2 = 128-byte swizzle (bits
+// 61-63).  The K steps of 16 values inside a 128-byte row advance the start
+// address by 32 B; the swizzle is applied to the final address bits.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, BF16
@@ -69,166 +96,19 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
          (static_cast<uint32_t>(m >> 4) << 24);
 }
 
-// Element offsets (in BF16 values) of the tiled layouts described above.
+// Element offset (in BF16 values) of (row r, K value c) inside one swizzled
+// 64-wide K slice, and of the tiled layouts described above.
+__host__ __device__ __forceinline__ int sw128_offset(int r, int c) {
+  return r * 64 + (((c >> 3) ^ (r & 7)) << 3) + (c & 7);
+}
 __host__ __device__ __forceinline__ size_t wt_offset(int row, int col, int Kpad) {
   const size_t tile = static_cast<size_t>(row / kSwM) * (Kpad / kSwK) + col / kSwK;
-  const int r = row % kSwM, c = col % kSwK;
-  return tile * (kSwM * kSwK) + ((c / 8) * (kSwM / 8) * 128 + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2) / 2;
+  return tile * (kSwM * kSwK) + sw128_offset(row % kSwM, col % kSwK);
 }
-__host__ __device__ __forceinline__ size_t xt_offset(int res, int kcol, int Kpad) {
-  const size_t tile = static_cast<size_t>(res / kSwN) * (2 * Kpad / kSwK) + kcol / kSwK;
-  const int r = res % kSwN, c = kcol % kSwK;
-  return tile * (kSwN * kSwK) + ((c / 8) * (kSwN / 8) * 128 + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2) / 2;
+__host__ __device__ __forceinline__ size_t xt_offset(int res, int kcol, int Kpad, int bn) {
+  const size_t tile = static_cast<size_t>(res / bn) * (2 * Kpad / kSwK) + kcol / kSwK;
+  return tile * (static_cast<size_t>(bn) * kSwK) + sw128_offset(res % bn, kcol % kSwK);
 }
-
-// One 128 x 64 tile of D = W X_hi + W X_lo per CTA; writes D^T.
-// Thread 0 streams K slices (one W tile and the matching X_hi and X_lo
-// tiles) with bulk copies into a ring (full / empty mbarriers) and issues the
-// MMAs, each W slice serving both halves; all four warps then read the
-// accumulator from tensor memory.
-__global__ void __launch_bounds__(kSwThreads) sweep_gemm_kernel(const __grid_constant__ GemmArgs g) {
-  extern __shared__ __align__(128) unsigned char sw_smem[];
-  unsigned char* smem = sw_smem;
-  __shared__ uint64_t full[kSwSlots], empty[kSwSlots], done;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_ok;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kSwM, n0 = blockIdx.y * kSwN;
-  const int nk = g.Kpad / kSwK;       // K slices of W
-  auto slotA = [&](int s) { return smem + s * kSwSlot; };
-  auto slotB = [&](int s) { return smem + s * kSwSlot + kSwSliceA; };  // X_hi, then X_lo
-
-  if (tid == 0) {
-    for (int s = 0; s < kSwSlots; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(&done, 1);
-    s_ok = 1;
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base)),
-                 "n"(kSwN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-
-  if (tid == 0) {
-    constexpr uint32_t idesc = umma_idesc_bf16(kSwM, kSwN);
-    const __nv_bfloat16* wtile = g.Wb + static_cast<size_t>(blockIdx.x) * nk * (kSwM * kSwK);
-    const __nv_bfloat16* xtile = g.Xs + static_cast<size_t>(blockIdx.y) * 2 * nk * (kSwN * kSwK);
-    const uint64_t pol = policy_evict_last();
-    bool ok = true;
-    int p = 0;  // next slice to load
-    int c = 0;  // next slice to multiply
-    for (; c < nk && ok; ++c) {
-      while (p < nk && p < c + kSwSlots) {
-        const int s = p % kSwSlots;
-        if (p >= kSwSlots && !mbar_wait_bounded(&empty[s], ((p / kSwSlots) - 1) & 1, g.timeout_ns, nullptr)) {
-          ok = false;
-          break;
-        }
-        mbar_arrive_expect_tx(&full[s], kSwSlot);
-        bulk_g2s(slotA(s), wtile + static_cast<size_t>(p) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
-        bulk_g2s(slotB(s), xtile + static_cast<size_t>(p) * (kSwN * kSwK), kSwSliceB, &full[s], pol);
-        bulk_g2s(slotB(s) + kSwSliceB, xtile + static_cast<size_t>(nk + p) * (kSwN * kSwK), kSwSliceB,
-                 &full[s], pol);
-        ++p;
-      }
-      if (!ok) break;
-      const int s = c % kSwSlots;
-      if (!mbar_wait_bounded(&full[s], (c / kSwSlots) & 1, g.timeout_ns, nullptr)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(slotA(s)), b0 = smem_u32(slotB(s));
-#pragma unroll
-      for (int j = 0; j < 2 * (kSwK / 16); ++j) {
-        const int jk = j % (kSwK / 16), half = j / (kSwK / 16);  // X_hi, then X_lo
-        const uint64_t ad = umma_desc(a0 + jk * 2 * (kSwM / 8) * 128, (kSwM / 8) * 128, 128);
-        const uint64_t bd = umma_desc(b0 + half * kSwSliceB + jk * 2 * (kSwN / 8) * 128,
-                                      (kSwN / 8) * 128, 128);
-        const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&empty[s]))
-          : "memory");
-    }
-    if (!ok) {
-      report_error(g.err, kErrTimeout, blockIdx.x, 0u, kSiteFull);
-      s_ok = 0;
-      // copies still in flight land before the CTA leaves
-      for (int q = c; q < p; ++q)
-        mbar_wait_bounded(&full[q % kSwSlots], (q / kSwSlots) & 1, g.timeout_ns, nullptr);
-    }
-    // completion of every MMA issued above
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&done))
-        : "memory");
-  }
-  const bool fin = mbar_wait_bounded(&done, 0u, g.timeout_ns, nullptr);
-  const bool ok = __syncthreads_and(fin) && s_ok;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
-    const int k = m0 + 32 * warp + lane;
-#pragma unroll
-    for (int c0 = 0; c0 < kSwN; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-            "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (k < g.N) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int r = n0 + c0 + j;
-          if (r < g.R) g.Dt[static_cast<size_t>(r) * g.N + k] = __uint_as_float(v[j]);
-        }
-      }
-    }
-  } else if (!fin && tid == 0) {
-    report_error(g.err, kErrTimeout, blockIdx.x, 0u, kSiteDrain);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kSwN) : "memory");
-}
-
-struct EpiArgs {
-  const float* Dt;          // [R][N]
-  const float* w_in;        // N x n_in (shared)
-  const float* u;           // T x n_in
-  const int* t_dev;         // current input sample (device counter)
-  float2* mn;               // [3][R][N] df
-  float2* ms;
-  float2* ksum;
-  __nv_bfloat16* Xs;        // Xt tiles
-  float* states_out;        // [T][R][N] or nullptr
-  const df* hs0_r;          // per reservoir H_s0
-  const df* ain_g_r;        // per reservoir g A_in
-  int N, R, Kpad, n_in, comp, st, last_sub;
-  KArgs c;                  // shared constants (gdt, alpha, happl, hkp, lambda, p, acp, sixth)
-};
 
 // dt * dm/dt of Eq. (gov) for one oscillator in double-float, with the
 // reservoir's own H_s0 and the full x-field hx (coupling + input).
@@ -249,42 +129,25 @@ __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df
   for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_add(t[i], df_mul(c.alpha, u[i])));
 }
 
-// One (reservoir, oscillator) pair per thread: finish stage st with the
-// coupling sum from the product, combine RK4, publish the next stage value
-// into X (hi and lo BF16 parts) and sample at the end of an input sample.
-// Each stage reads and writes only the state it needs: stage 0 evaluates at
-// m_n and writes (sum, stage state); stages 1-2 update both; stage 3 writes
-// m_{n+1} only (the next stage 0 starts from it).
-__global__ void __launch_bounds__(256) sweep_epilogue_kernel(const __grid_constant__ EpiArgs e) {
-  // R N <= 2^31 (checked at create): 32-bit index arithmetic
-  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<unsigned>(e.R) * static_cast<unsigned>(e.N)) return;
-  const unsigned r = idx / static_cast<unsigned>(e.N), k = idx - r * static_cast<unsigned>(e.N);
-  const size_t RN = static_cast<size_t>(e.R) * e.N;
-  const int t = *e.t_dev;
-  const int st = e.st;
-  df mn[3], ms[3], ks[3];
+// Finish stage st of pair (reservoir r, oscillator k) with the coupling sum
+// hraw, given the pair's state (mn; ms and ks when st > 0) and the input
+// drive w_in . u_t of oscillator k: the RK4 combination, the next stage's X
+// (hi and lo BF16 terms, at element offsets xo and xo + lo_off of Xn) and the
+// sample at the end of an input sample.  Each stage writes only the state the
+// next one reads: stages 0-2 write (sum, stage state); stage 3 writes m_{n+1}
+// only (the next stage 0 starts from it).
+__device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsigned k, float hraw,
+                                           int st, int t, bool sample, df drive, df mn[3], df ms[3],
+                                           df ks[3], __nv_bfloat16* Xn, size_t xo, size_t lo_off) {
+  const size_t RN = static_cast<size_t>(a.R) * a.N;
+  const size_t idx = static_cast<size_t>(r) * a.N + k;
+  if (st == 0) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float2 a = e.mn[i * RN + idx];
-    mn[i] = df{a.x, a.y};
-    if (st > 0) {
-      const float2 b = e.ms[i * RN + idx], c = e.ksum[i * RN + idx];
-      ms[i] = df{b.x, b.y};
-      ks[i] = df{c.x, c.y};
-    } else {
-      ms[i] = mn[i];
-    }
+    for (int i = 0; i < 3; ++i) ms[i] = mn[i];
   }
-  // input drive w_in . u_t in double-float (each product exact), no FP64:
-  // that pipe runs at 1/64 of the FP32 rate here
-  df s = two_prod(e.w_in[static_cast<size_t>(k) * e.n_in], e.u[static_cast<size_t>(t) * e.n_in]);
-  for (int j = 1; j < e.n_in; ++j)
-    s = df_add(s, two_prod(e.w_in[static_cast<size_t>(k) * e.n_in + j],
-                           e.u[static_cast<size_t>(t) * e.n_in + j]));
-  const df hx = df_add(df_mul_f(e.c.acp, e.Dt[idx]), df_mul(e.ain_g_r[r], s));
+  const df hx = df_add(df_mul_f(a.c.acp, hraw), df_mul(a.ain_g_r[r], drive));
   df d[3];
-  sweep_increment(e.c, e.hs0_r[r], ms, hx, d);
+  sweep_increment(a.c, a.hs0_r[r], ms, hx, d);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (st == 0) {
@@ -298,42 +161,380 @@ __global__ void __launch_bounds__(256) sweep_epilogue_kernel(const __grid_consta
       ms[i] = df_add(mn[i], d[i]);
     } else {
       ks[i] = df_add(ks[i], d[i]);
-      mn[i] = df_add(mn[i], df_mul(ks[i], e.c.sixth));
+      mn[i] = df_add(mn[i], df_mul(ks[i], a.c.sixth));
       ms[i] = mn[i];
     }
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (st == 3) {
-      e.mn[i * RN + idx] = make_float2(mn[i].hi, mn[i].lo);
+      a.mn[i * RN + idx] = make_float2(mn[i].hi, mn[i].lo);
     } else {
-      e.ms[i * RN + idx] = make_float2(ms[i].hi, ms[i].lo);
-      e.ksum[i * RN + idx] = make_float2(ks[i].hi, ks[i].lo);
+      a.ms[i * RN + idx] = make_float2(ms[i].hi, ms[i].lo);
+      a.ksum[i * RN + idx] = make_float2(ks[i].hi, ks[i].lo);
     }
   }
-  // next stage value, split into two BF16 terms
   const float x = ms[0].hi;
   const __nv_bfloat16 xh = __float2bfloat16_rn(x);
   const __nv_bfloat16 xl = __float2bfloat16_rn(x - __bfloat162float(xh));
-  e.Xs[xt_offset(r, k, e.Kpad)] = xh;
-  e.Xs[xt_offset(r, e.Kpad + k, e.Kpad)] = xl;
-  if (st == 3 && e.last_sub && e.states_out)
-    e.states_out[static_cast<size_t>(t) * RN + idx] = mn[e.comp].hi;
+  Xn[xo] = xh;
+  Xn[xo + lo_off] = xl;
+  if (st == 3 && sample && a.states_out)
+    a.states_out[static_cast<size_t>(t) * RN + idx] = mn[a.comp].hi;
 }
 
-// Initial X from the stage state (ms) of every pair.
-__global__ void sweep_publish_kernel(const float2* ms, __nv_bfloat16* Xs, int N, int R, int Kpad) {
+// Asynchronous 8-byte global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Shared-memory staging of one pair's state per epilogue lane: mn, ms, ks
+// (3 float2 each).
+constexpr int kSpStageBytes = 9 * 8 * 32;                  // per epilogue warp
+constexpr int kSpStageAll = kSpStageBytes * kSpEpiWarps;   // 64.5 KB
+constexpr int kSpAlignSlack = 1024;                        // room to align the ring
+
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// The whole sweep call: 4 S T stages, tiles of this CTA in each.  Warp 0
+// (one thread) waits for the grid barrier, releases the stage to the copy
+// warps and issues the MMAs; warps 1-3 (one thread each) fill their ring
+// slots; warps 4-31 run the epilogue.
+__global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
+  // the swizzle pattern repeats every 1024 B: the ring starts on such a boundary
+  unsigned char* sp_smem = sp_smem_raw + ((1024u - (smem_u32(sp_smem_raw) & 1023u)) & 1023u);
+  __shared__ uint64_t full[kSpMaxSlots], empty[kSpMaxSlots], acc_full[2], acc_empty[2];
+  __shared__ uint64_t stage_done, stage_go, drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int n_tiles = a.tiles_m * a.tiles_n;
+  const int n_my = cta < n_tiles ? (n_tiles - 1 - cta) / G + 1 : 0;
+  const int nk = a.Kpad / kSwK;
+  const int L = n_my * nk;  // K slices of this CTA per stage
+  const uint32_t sliceB = static_cast<uint32_t>(a.bn) * kSwK * 2;  // one X slice (hi or lo)
+  const uint32_t slot_bytes = kSwSliceA + 2 * sliceB;
+  const long long n_stages = 4LL * a.S * a.T;
+  const volatile int* abort_flag = &s_abort;
+
+  if (tid == 0) {
+    for (int s = 0; s < a.slots; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kSpEpiWarps);
+    }
+    mbar_init(&stage_done, kSpEpiWarps);
+    mbar_init(&stage_go, 1);
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(2u * a.acc_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------- grid barrier and MMAs
+      const uint32_t idesc = umma_idesc_bf16(kSwM, 2 * a.bn);  // [X_hi | X_lo] rows
+      long long tiles_done = 0;  // accumulator sequence number of the stage's first tile
+      bool ok = true;
+      for (long long g = 0; g < n_stages && ok; ++g) {
+        if (g > 0) {
+          // grid barrier: this CTA's epilogue of stage g-1 is done (its X
+          // for stage g written), then every CTA's
+          if (n_my > 0 &&
+              !mbar_wait_bounded(&stage_done, static_cast<uint32_t>((g - 1) & 1), a.timeout_ns, abort_flag)) {
+            ok = false;
+            break;
+          }
+          red_release_add(a.gbar, 1ull);
+          const unsigned long long target = static_cast<unsigned long long>(G) * static_cast<unsigned long long>(g);
+          const unsigned long long t0 = gtimer();
+          for (uint32_t n = 1; ld_acquire_u64(a.gbar) < target; ++n) {
+            if ((n & 31u) == 0) {
+              if (ld_relaxed_i32(a.err) != 0 || gtimer() - t0 > a.timeout_ns) {
+                ok = false;
+                break;
+              }
+            }
+          }
+          if (!ok) break;
+          fence_proxy_async_global();
+        }
+        mbar_arrive(&stage_go);  // the copy warps may read this stage's X
+        const long long base = g * L;
+        for (int lq = 0; lq < L; ++lq) {
+          const int i = lq / nk, j = lq % nk;
+          const long long seq = tiles_done + i;
+          const int b = static_cast<int>(seq & 1);
+          if (j == 0 && seq >= 2) {
+            // the epilogue has read this accumulator's previous tile
+            if (!mbar_wait_bounded(&acc_empty[b], static_cast<uint32_t>(((seq >> 1) - 1) & 1), a.timeout_ns,
+                                   abort_flag)) {
+              ok = false;
+              break;
+            }
+          }
+          const long long Q = base + lq;
+          const int s = static_cast<int>(Q % a.slots);
+          if (!mbar_wait_bounded(&full[s], static_cast<uint32_t>((Q / a.slots) & 1), a.timeout_ns, abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sp_smem + static_cast<size_t>(s) * slot_bytes);
+          const uint32_t b0 = a0 + kSwSliceA;
+          const uint32_t dt = tmem + static_cast<uint32_t>(b * a.acc_cols);
+#pragma unroll
+          for (int jk = 0; jk < kSwK / 16; ++jk) {
+            // B: the X_hi slice and the X_lo slice behind it, 2 bn rows
+            const uint64_t ad = umma_desc_sw128(a0 + jk * 32);
+            const uint64_t bd = umma_desc_sw128(b0 + jk * 32);
+            const uint32_t accum = (j > 0 || jk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                : "memory");
+          }
+          umma_commit(&empty[s]);
+          if (j == nk - 1) umma_commit(&acc_full[b]);
+        }
+        tiles_done += n_my;
+      }
+      if (!ok) {
+        if (!*abort_flag) report_error(a.err, kErrTimeout, cta, 0u, kSiteFull);
+        s_abort = 1;
+        // never leave with MMAs in flight
+        umma_commit(&drain);
+        mbar_wait_bounded(&drain, 0u, a.timeout_ns, nullptr);
+      }
+    }
+  } else if (warp < kSpEpiFirst) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ copies
+      // this warp owns positions P = pid (mod kSpProducers), hence ring
+      // slots P % slots = pid (mod kSpProducers): slots is a multiple of it
+      const int pid = warp - 1;
+      const uint64_t pol = policy_evict_last();
+      long long last = -1;  // last position issued
+      bool ok = true;
+      for (long long g = 0; g < n_stages && ok; ++g) {
+        if (!mbar_wait_bounded(&stage_go, static_cast<uint32_t>(g & 1), a.timeout_ns, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const __nv_bfloat16* X = (g & 1) ? a.X1 : a.X0;
+        const long long base = g * L;
+        const int lp0 = static_cast<int>(((pid - base % kSpProducers) % kSpProducers + kSpProducers) % kSpProducers);
+        for (int lp = lp0; lp < L; lp += kSpProducers) {
+          const long long P = base + lp;
+          const int s = static_cast<int>(P % a.slots);
+          if (P >= a.slots &&
+              !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((P / a.slots) - 1) & 1), a.timeout_ns,
+                                 abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int i = lp / nk, j = lp % nk;
+          const int tile = cta + i * G;
+          const int tm = tile % a.tiles_m, tn = tile / a.tiles_m;
+          unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
+          const __nv_bfloat16* xt = X + static_cast<size_t>(tn) * 2 * nk * (a.bn * kSwK);
+          mbar_arrive_expect_tx(&full[s], slot_bytes);
+          bulk_g2s(slot, a.Wb + (static_cast<size_t>(tm) * nk + j) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
+          bulk_g2s(slot + kSwSliceA, xt + static_cast<size_t>(j) * (a.bn * kSwK), sliceB, &full[s], pol);
+          bulk_g2s(slot + kSwSliceA + sliceB, xt + static_cast<size_t>(nk + j) * (a.bn * kSwK), sliceB,
+                   &full[s], pol);
+          last = P;
+        }
+      }
+      if (!ok) {
+        if (!*abort_flag) report_error(a.err, kErrTimeout, cta, 0u, kSiteEmpty);
+        s_abort = 1;
+      }
+      // never leave with copies in flight: the latest use of each own slot
+      for (long long P = last; P >= 0 && P > last - a.slots; P -= kSpProducers)
+        if (!mbar_wait_bounded(&full[P % a.slots], static_cast<uint32_t>((P / a.slots) & 1), a.timeout_ns, nullptr)) {
+          report_error(a.err, kErrTimeout, cta, 0u, kSiteDrain);
+          break;
+        }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q4 = warp & 3;                      // TMEM lanes 32 q4 .. 32 q4 + 31
+    const int wi = (warp - kSpEpiFirst) >> 2;     // 0 .. kSpEpiPerQuarter - 1
+    const uint32_t lane_base = static_cast<uint32_t>(32 * q4) << 16;
+    const size_t lo_off = static_cast<size_t>(nk) * a.bn * kSwK;  // X_lo slices follow X_hi
+    const size_t RN = static_cast<size_t>(a.R) * a.N;
+    float2* stg = reinterpret_cast<float2*>(sp_smem + static_cast<size_t>(a.slots) * slot_bytes +
+                                            static_cast<size_t>(warp - kSpEpiFirst) * kSpStageBytes);
+    long long seq = 0;
+    bool ok = true;
+    // a CTA without tiles has no epilogue (the host never plans one)
+    for (long long g = 0; g < n_stages && ok && n_my > 0; ++g) {
+      const int st = static_cast<int>(g & 3);
+      const long long step = g >> 2;
+      const int t = static_cast<int>(step / a.S);
+      const bool sample = (step % a.S) == a.S - 1;
+      __nv_bfloat16* Xn = (g & 1) ? a.X0 : a.X1;  // the next stage's operand
+      for (int i = 0; i < n_my; ++i, ++seq) {
+        const int tile = cta + i * G;
+        const int tm = tile % a.tiles_m, tn = tile / a.tiles_m;
+        const int b = static_cast<int>(seq & 1);
+        const unsigned k = static_cast<unsigned>(tm * kSwM + 32 * q4 + lane);
+        const bool row_ok = k < static_cast<unsigned>(a.N);
+        // X offset of (reservoir tn*bn + jcol, oscillator k), hi term: slice
+        // base + sw128_offset(jcol, k % 64)
+        const size_t xk = (static_cast<size_t>(tn) * 2 * nk + (k >> 6)) * (a.bn * kSwK) + (k & 7u);
+        const unsigned kchunk = (k & 63u) >> 3;
+        // input drive of oscillator k for this sample (the same for every reservoir)
+        df drive{0.f, 0.f};
+        if (row_ok) {
+          drive = two_prod(a.w_in[static_cast<size_t>(k) * a.n_in], a.u[static_cast<size_t>(t) * a.n_in]);
+          for (int jj = 1; jj < a.n_in; ++jj)
+            drive = df_add(drive, two_prod(a.w_in[static_cast<size_t>(k) * a.n_in + jj],
+                                           a.u[static_cast<size_t>(t) * a.n_in + jj]));
+        }
+        // the state of the next column's pair is copied into shared memory
+        // while the current one is computed
+        auto prefetch = [&](int jc) {
+          if (!a.staged) return;
+          const unsigned r = static_cast<unsigned>(tn * a.bn + jc);
+          if (row_ok && r < static_cast<unsigned>(a.R)) {
+            const size_t idx = static_cast<size_t>(r) * a.N + k;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              cp_async8(stg + (q * 32 + lane), a.mn + q * RN + idx);
+              if (st > 0) {
+                cp_async8(stg + ((3 + q) * 32 + lane), a.ms + q * RN + idx);
+                cp_async8(stg + ((6 + q) * 32 + lane), a.ksum + q * RN + idx);
+              }
+            }
+          }
+          cp_async_commit();
+        };
+        prefetch(wi);  // overlaps the tile's MMAs
+        const bool landed = mbar_wait_bounded(&acc_full[b], static_cast<uint32_t>((seq >> 1) & 1), a.timeout_ns,
+                                              abort_flag);
+        if (!__all_sync(0xffffffffu, landed)) {
+          cp_async_wait_all();
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int jc = wi; jc < a.bn; jc += kSpEpiPerQuarter) {
+          uint32_t vh, vl;  // W X_hi and W X_lo of this pair
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                       : "=r"(vh)
+                       : "r"(tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols + jc)));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                       : "=r"(vl)
+                       : "r"(tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols + a.bn + jc)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const float hraw = __fadd_rn(__uint_as_float(vh), __uint_as_float(vl));
+          const unsigned r = static_cast<unsigned>(tn * a.bn + jc);
+          const bool pair_ok = row_ok && r < static_cast<unsigned>(a.R);
+          df mn[3], ms[3], ks[3];
+          if (a.staged) {
+            cp_async_wait_all();
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const float2 x0 = stg[q * 32 + lane];
+              mn[q] = df{x0.x, x0.y};
+              if (st > 0) {
+                const float2 x1 = stg[(3 + q) * 32 + lane], x2 = stg[(6 + q) * 32 + lane];
+                ms[q] = df{x1.x, x1.y};
+                ks[q] = df{x2.x, x2.y};
+              }
+            }
+            if (jc + kSpEpiPerQuarter < a.bn) prefetch(jc + kSpEpiPerQuarter);
+          } else if (pair_ok) {
+            const size_t idx = static_cast<size_t>(r) * a.N + k;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const float2 x0 = a.mn[q * RN + idx];
+              mn[q] = df{x0.x, x0.y};
+              if (st > 0) {
+                const float2 x1 = a.ms[q * RN + idx], x2 = a.ksum[q * RN + idx];
+                ms[q] = df{x1.x, x1.y};
+                ks[q] = df{x2.x, x2.y};
+              }
+            }
+          }
+          if (pair_ok) {
+            const size_t xo = xk + static_cast<size_t>(jc * 64 + ((kchunk ^ (jc & 7u)) << 3));
+            sweep_pair(a, r, k, hraw, st, t, sample, drive, mn, ms, ks, Xn, xo, lo_off);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
+      }
+      if (!ok) break;
+      fence_proxy_async_global();  // this stage's X writes, before the copies of the next
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&stage_done);
+    }
+    if (!ok && lane == 0) {
+      if (!*abort_flag) report_error(a.err, kErrTimeout, cta, 0u, kSiteFull);
+      s_abort = 1;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * a.acc_cols)
+                 : "memory");
+  }
+}
+
+// X of the current stage from the stage state (ms) of every pair.
+__global__ void sweep_publish_kernel(const float2* ms, __nv_bfloat16* Xs, int N, int R, int Kpad, int bn) {
   const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (idx >= static_cast<long long>(R) * N) return;
   const int r = static_cast<int>(idx / N), k = static_cast<int>(idx % N);
   const float x = ms[idx].x;
   const __nv_bfloat16 xh = __float2bfloat16_rn(x);
   const __nv_bfloat16 xl = __float2bfloat16_rn(x - __bfloat162float(xh));
-  Xs[xt_offset(r, k, Kpad)] = xh;
-  Xs[xt_offset(r, Kpad + k, Kpad)] = xl;
+  Xs[xt_offset(r, k, Kpad, bn)] = xh;
+  Xs[xt_offset(r, Kpad + k, Kpad, bn)] = xl;
 }
-
-__global__ void sweep_advance_kernel(int* t_dev) { *t_dev += 1; }
 
 // W (float, N x N row-major) -> BF16 Wt tiles (zeroed beforehand).
 __global__ void sweep_pack_w_kernel(const float* W, __nv_bfloat16* Wb, int N, int Kpad) {

@@ -47,6 +47,16 @@ class sto_config(ctypes.Structure):
                 ("l2_keep_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class sto_batch_plan(ctypes.Structure):
+    _fields_ = [("tile_n", ctypes.c_int32), ("slots", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("tiles", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("tuned_us_per_stage", ctypes.c_float),
+                ("staged", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+
+
 class sto_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("grid", ctypes.c_int32), ("rows_max", ctypes.c_int32),
                 ("panel_cols", ctypes.c_int32), ("panels", ctypes.c_int32),
@@ -91,6 +101,8 @@ SIGNATURES = {
     "sto_run_batched": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "sto_batch_get_state": (ctypes.c_int, [_VP, _VP]),
     "sto_batch_destroy": (None, [_VP]),
+    "sto_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32]),
+    "sto_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(sto_batch_plan)]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
 }
@@ -436,6 +448,15 @@ class Sweep:
         out = np.empty((self.R, 3, self.N), dtype=np.float64)
         _check(load_library().sto_batch_get_state(self.handle, out.ctypes.data))
         return out
+
+    def set_plan(self, tile_n: int = 0, slots: int = 0):
+        """Force a tile width / ring depth, or (0, 0) to run the autotuner."""
+        _check(load_library().sto_batch_set_plan(self.handle, int(tile_n), int(slots)))
+
+    def plan(self) -> dict:
+        p = sto_batch_plan()
+        _check(load_library().sto_batch_get_plan(self.handle, ctypes.byref(p)))
+        return p.as_dict()
 
     def close(self):
         if self.handle:

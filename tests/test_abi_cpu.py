@@ -62,7 +62,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors vs the C compiler's sizeof / offsetof of include/sto.h."""
     fields = {"sto_params": [f[0] for f in sto.sto_params._fields_],
               "sto_config": [f[0] for f in sto.sto_config._fields_],
-              "sto_info": [f[0] for f in sto.sto_info._fields_]}
+              "sto_info": [f[0] for f in sto.sto_info._fields_],
+              "sto_batch_plan": [f[0] for f in sto.sto_batch_plan._fields_],
+              "sto_grads": [f[0] for f in sto.sto_grads._fields_]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sto.h"', "int main(void){"]
     for st, names in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

@@ -115,3 +115,73 @@ def test_group_of_own_w_reservoirs_matches_separate_runs(sto):
     _, orc = oracle.run(oracle_params(params[0]), W.astype(np.float64), w_in.astype(np.float64),
                         m0.astype(np.float64), u.astype(np.float64))
     assert np.max(np.abs(outs[0] - orc)) <= 1e-5
+
+
+@pytest.mark.parametrize("tile_n,slots", [(16, 3), (32, 6), (48, 3), (80, 3), (80, 6), (112, 3), (128, 3)])
+def test_sweep_forced_plans_match_oracle(sto, tile_n, slots):
+    """Every tile width and ring depth gives the oracle's states (ragged N and R)."""
+    N, R, T = 300, 70, 2
+    W, w_in, _, u = make_system(N, "gauss", seed=11, T=T)
+    rng = np.random.default_rng(11)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=3, A_cp=100.0, A_in=30.0)
+    st = np.zeros((T, R, N), np.float32)
+    with sto.Sweep(W, w_in, P, currents=cur, gains=gain) as sw:
+        sw.set_plan(tile_n, slots)
+        plan = sw.plan()
+        assert (plan["tile_n"], plan["slots"], plan["tuned"]) == (tile_n, slots, 0)
+        assert plan["staged"] in (0, 1)
+        assert plan["tiles"] == -(-N // 128) * -(-R // tile_n)
+        sw.run(u, st)
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, 17, 33, 64, 69):
+        OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(st[:, r] - ref)) <= 1e-5, r
+
+
+def test_sweep_several_tiles_per_cta(sto):
+    """More tiles than SMs: each CTA finishes several tiles per stage,
+    alternating between its two tensor-memory accumulators."""
+    N, R, T = 256, 2400, 2
+    W, w_in, _, u = make_system(N, "gauss", seed=12, T=T)
+    rng = np.random.default_rng(12)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    P = sto.Params(substeps=2, A_cp=100.0, A_in=30.0)
+    st = np.zeros((T, R, N), np.float32)
+    with sto.Sweep(W, w_in, P, currents=cur) as sw:
+        sw.set_plan(16, 3)
+        plan = sw.plan()
+        assert plan["tiles"] == 2 * 150 and plan["tiles"] > plan["grid"]
+        sw.run(u, st)
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, 1, 799, 1500, 2399):
+        OP = oracle_params(P.replace(current=float(cur[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(st[:, r] - ref)) <= 1e-5, r
+
+
+def test_sweep_autotuner_and_invalid_plans(sto):
+    N, R, T = 500, 130, 1
+    W, w_in, _, u = make_system(N, "gauss", seed=13, T=T)
+    P = sto.Params(substeps=2)
+    with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw:
+        assert sw.plan()["tile_n"] == 0  # no plan before the first run
+        with pytest.raises(sto.StoError):
+            sw.set_plan(40, 3)  # not a multiple of 16
+        with pytest.raises(sto.StoError):
+            sw.set_plan(64, 9)  # ring deeper than the kernel allows
+        st = np.zeros((T, R, N), np.float32)
+        sw.run(u, st)
+        plan = sw.plan()
+        assert plan["tuned"] == 1 and plan["candidates"] >= 1 and plan["tuned_us_per_stage"] > 0
+        assert plan["tile_n"] % 16 == 0 and plan["grid"] <= torch.cuda.get_device_properties(0).multi_processor_count
+        # the tuner restored the state it ran from: same samples as a forced plan
+        ref = np.zeros_like(st)
+        with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw2:
+            sw2.set_plan(plan["tile_n"], plan["slots"])
+            sw2.run(u, ref)
+        assert np.array_equal(st, ref)
