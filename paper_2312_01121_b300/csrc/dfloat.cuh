@@ -92,6 +92,19 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
   return fast_two_sum(p.hi, p.lo);
 }
 
+// a * b without the final renormalisation: hi + lo carries the product to
+// the same accuracy as df_mul, with |lo| up to a few ulp(hi).  Only an
+// operand of df_add / df_mul (which renormalise), never a stored value.
+__device__ __forceinline__ df df_mul_raw(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return p;
+}
+
+// c + a * b.
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(c, df_mul_raw(a, b)); }
+
 // Exact scaling by a power of two.
 __device__ __forceinline__ df df_scale2(df a, float pow2) {
   return {__fmul_rn(a.hi, pow2), __fmul_rn(a.lo, pow2)};
@@ -99,7 +112,24 @@ __device__ __forceinline__ df df_scale2(df a, float pow2) {
 
 // a*b - c*d (one component of a cross product).
 __device__ __forceinline__ df df_cross1(df a, df b, df c, df d) {
-  return df_sub(df_mul(a, b), df_mul(c, d));
+  return df_sub(df_mul_raw(a, b), df_mul_raw(c, d));
+}
+
+// Terms of the spin-torque field that depend on the polarizer p: m . p and
+// p x m.  The paper's p = (1, 0, cos 90 deg) has p_y = 0 exactly; its terms
+// are then left out (a uniform branch on a launch constant).
+__device__ __forceinline__ void df_p_terms(df px, df py, df pz, const df m[3], df* s, df c[3]) {
+  if (py.hi == 0.f && py.lo == 0.f) {
+    *s = df_add(df_mul_raw(m[0], px), df_mul_raw(m[2], pz));
+    c[0] = df_neg(df_mul(pz, m[1]));
+    c[1] = df_cross1(pz, m[0], px, m[2]);
+    c[2] = df_mul(px, m[1]);
+  } else {
+    *s = df_add(df_add(df_mul_raw(m[0], px), df_mul_raw(m[1], py)), df_mul_raw(m[2], pz));
+    c[0] = df_cross1(py, m[2], pz, m[1]);
+    c[1] = df_cross1(pz, m[0], px, m[2]);
+    c[2] = df_cross1(px, m[1], py, m[0]);
+  }
 }
 
 // 1 / b: float reciprocal refined by one Newton step in df.

@@ -261,13 +261,11 @@ __device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag
 // formed while the CTA waits for the other oscillators' m^x; once the
 // coupling field is known the increment costs three df multiply-adds.
 __device__ __forceinline__ void llg_affine(const KArgs& a, const df m[3], df A[3], df B[3]) {
-  const df s = df_add(df_add(df_mul(m[0], a.px), df_mul(m[1], a.py)), df_mul(m[2], a.pz));  // m.p
+  df s, c[3];                                                                               // m.p, p x m
+  df_p_terms(a.px, a.py, a.pz, m, &s, c);
   const df hs = df_mul(a.hs0, df_rcp(df_add_f(df_mul(a.lambda, s), 1.0f)));              // H_s(m)
-  const df cx = df_cross1(a.py, m[2], a.pz, m[1]);                                          // p x m
-  const df cy = df_cross1(a.pz, m[0], a.px, m[2]);
-  const df cz = df_cross1(a.px, m[1], a.py, m[0]);
-  const df b[3] = {df_mul(hs, cx), df_mul(hs, cy),                                          // b0
-                   df_add(df_add(a.happl, df_mul(a.hkp, m[2])), df_mul(hs, cz))};
+  const df b[3] = {df_mul(hs, c[0]), df_mul(hs, c[1]),                                      // b0
+                   df_fma(hs, c[2], df_fma(a.hkp, m[2], a.happl))};
   const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]),                                       // m x b0
                    df_cross1(m[2], b[0], m[0], b[2]),
                    df_cross1(m[0], b[1], m[1], b[0])};
@@ -275,12 +273,12 @@ __device__ __forceinline__ void llg_affine(const KArgs& a, const df m[3], df A[3
                    df_cross1(m[2], t[0], m[0], t[2]),
                    df_cross1(m[0], t[1], m[1], t[0])};
   const df e[3] = {df{0.f, 0.f}, m[2], df_neg(m[1])};                                       // m x e_x
-  const df v[3] = {df_neg(df_add(df_mul(m[1], m[1]), df_mul(m[2], m[2]))),                 // m x (m x e_x)
+  const df v[3] = {df_neg(df_add(df_mul_raw(m[1], m[1]), df_mul_raw(m[2], m[2]))),         // m x (m x e_x)
                    df_mul(m[0], m[1]), df_mul(m[0], m[2])};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    A[i] = df_mul(a.gdt, df_add(t[i], df_mul(a.alpha, u[i])));
-    B[i] = df_mul(a.gdt, df_add(e[i], df_mul(a.alpha, v[i])));
+    A[i] = df_mul(a.gdt, df_fma(a.alpha, u[i], t[i]));
+    B[i] = df_mul(a.gdt, df_fma(a.alpha, v[i], e[i]));
   }
 }
 
@@ -348,7 +346,7 @@ struct ForwardProgram {
     const df hx = df_add(df_mul_f(a.acp, hraw), hin);
     df d[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = df_add(fa[i], df_mul(hx, fb[i]));
+    for (int i = 0; i < 3; ++i) d[i] = df_fma(hx, fb[i], fa[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       if (st == 0) {
@@ -362,7 +360,7 @@ struct ForwardProgram {
         ms[i] = df_add(mn[i], d[i]);
       } else {
         ksum[i] = df_add(ksum[i], d[i]);
-        mn[i] = df_add(mn[i], df_mul(ksum[i], a.sixth));
+        mn[i] = df_fma(ksum[i], a.sixth, mn[i]);
         ms[i] = mn[i];
       }
     }

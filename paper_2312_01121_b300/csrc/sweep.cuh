@@ -114,19 +114,17 @@ __host__ __device__ __forceinline__ size_t xt_offset(int res, int kcol, int Kpad
 // reservoir's own H_s0 and the full x-field hx (coupling + input).
 __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df m[3], df hx,
                                                 df d[3]) {
-  const df s = df_add(df_add(df_mul(m[0], c.px), df_mul(m[1], c.py)), df_mul(m[2], c.pz));
+  df s, pm[3];
+  df_p_terms(c.px, c.py, c.pz, m, &s, pm);
   const df hs = df_mul(hs0, df_rcp(df_add_f(df_mul(c.lambda, s), 1.0f)));
-  const df cx = df_cross1(c.py, m[2], c.pz, m[1]);
-  const df cy = df_cross1(c.pz, m[0], c.px, m[2]);
-  const df cz = df_cross1(c.px, m[1], c.py, m[0]);
-  const df b[3] = {df_add(hx, df_mul(hs, cx)), df_mul(hs, cy),
-                   df_add(df_add(c.happl, df_mul(c.hkp, m[2])), df_mul(hs, cz))};
+  const df b[3] = {df_fma(hs, pm[0], hx), df_mul(hs, pm[1]),
+                   df_fma(hs, pm[2], df_fma(c.hkp, m[2], c.happl))};
   const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]), df_cross1(m[2], b[0], m[0], b[2]),
                    df_cross1(m[0], b[1], m[1], b[0])};
   const df u[3] = {df_cross1(m[1], t[2], m[2], t[1]), df_cross1(m[2], t[0], m[0], t[2]),
                    df_cross1(m[0], t[1], m[1], t[0])};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_add(t[i], df_mul(c.alpha, u[i])));
+  for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_fma(c.alpha, u[i], t[i]));
 }
 
 // Finish stage st of pair (reservoir r, oscillator k) with the coupling sum
@@ -145,7 +143,7 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
 #pragma unroll
     for (int i = 0; i < 3; ++i) ms[i] = mn[i];
   }
-  const df hx = df_add(df_mul_f(a.c.acp, hraw), df_mul(a.ain_g_r[r], drive));
+  const df hx = df_fma(a.ain_g_r[r], drive, df_mul_f(a.c.acp, hraw));
   df d[3];
   sweep_increment(a.c, a.hs0_r[r], ms, hx, d);
 #pragma unroll
@@ -161,7 +159,7 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
       ms[i] = df_add(mn[i], d[i]);
     } else {
       ks[i] = df_add(ks[i], d[i]);
-      mn[i] = df_add(mn[i], df_mul(ks[i], a.c.sixth));
+      mn[i] = df_fma(ks[i], a.c.sixth, mn[i]);
       ms[i] = mn[i];
     }
   }
