@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=1000)
     ap.add_argument("--adj-t", type=int, default=40, help="input samples per adjoint call")
     ap.add_argument("--adj-k", type=int, default=20, help="checkpoint interval (samples)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-ns", default="1000,10000",
+                    help="N of the FP64 replica of the paper's benchmark (comma separated)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed launches per FP64 case")
     return ap.parse_args()
 
 
@@ -406,6 +410,55 @@ def time_group(args, seed, torch, sto, dev, hbm_peak):
             "note": "W of every reservoir is at most 64 MB and is kept in L2 between stages"}
 
 
+def time_fp64(args, seed, torch, sto, dev, hbm_peak):
+    """The paper's own benchmark in its precision (Sec. 3.3, Table 1): FP64
+    coupling, u = 0, Eq. (initial) for every oscillator, W of the paper's
+    structure (zero diagonal, U[-1, 1], spectral radius ~1 by the circular
+    law), dt = 1e-11 s.  One launch = 100 RK4 steps; both products."""
+    from paper_2312_01121_b300 import inputs
+    out = []
+    stream = torch.cuda.current_stream()
+    for N in [int(x) for x in args.fp64_ns.split(",") if x]:
+        W = inputs.coupling_paper_circular(N, seed=seed)
+        w_in = inputs.f32(inputs.input_weights(N, 1, seed=seed))
+        Wd = torch.from_numpy(W).to(dev)
+        del W
+        S, K = args.substeps, args.fp64_steps
+        u_d = torch.zeros((1, 1), dtype=torch.float32, device=dev)
+        for coupling in ("df64", "f64"):
+            res = sto.Reservoir(Wd, torch.from_numpy(w_in).to(dev), sto.Params(substeps=S),
+                                stream=stream, coupling=coupling)
+            res.run(u_d, None)  # warm-up
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+            ev[0].record(stream)
+            for i in range(K):
+                res.run(u_d, None)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize()
+            per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+            m = res.state()
+            info = res.info()
+            res.close()
+            stages = 4 * S
+            ms = statistics.mean(per)
+            gbs = 8.0 * N * N * stages / (ms / 1e3) / 1e9
+            out.append({"N": N, "coupling": coupling, "us_per_stage": ms * 1e3 / stages,
+                        "value": N * S / (ms / 1e3), "unit": "node-updates/s",
+                        "w_gbs_algorithmic": gbs, "frac_of_hbm": gbs / hbm_peak,
+                        "seconds_per_5e3_rk4_steps": ms / 1e3 / S * 5e3,
+                        "max_abs_norm_minus_1": float(np.max(np.abs(np.linalg.norm(m, axis=0) - 1.0))),
+                        "grid": info["grid"], "resident": info["resident"]})
+        del Wd
+        torch.cuda.empty_cache()
+    return {"workload": "paper benchmark replica (Sec. 3.3, Table 1): FP64 coupling, u=0, "
+                        "Eq. (initial), paper-structured W, dt=1e-11 s; one launch = "
+                        f"{args.substeps} RK4 steps",
+            "products": {"df64": "W as exact FP32 pairs (48-bit), double-float products and sums",
+                         "f64": "W in FP64, FP64 fused multiply-adds"},
+            "cases": out}
+
+
 def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
     """Node-updates/s of the FP64 oracle on a bounded sample of the workload."""
     import oracle
@@ -498,6 +551,9 @@ def main():
     group = None
     if not args.no_group:
         group = time_group(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = time_fp64(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
 
     value, e2e_value, tot_ms, updates = combine_ranks(
         main_r["total_ms"], main_r.get("e2e_s"), main_r["node_updates"], world, reduce_max)
@@ -587,6 +643,8 @@ def main():
         line["sweep"] = sweep
     if group is not None:
         line["group"] = group
+    if fp64 is not None:
+        line["fp64"] = fp64
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -27,7 +27,10 @@
  *
  * Precision: W and the coupling matrix-vector product are FP32 (FP32
  * products, FP32 accumulation); the per-oscillator torque, the RK4 stage
- * combination and the state are FP64.  Sampled states are returned in FP32.
+ * combination and the state are FP64 (double-float on the FP32 pipes,
+ * about 48 significand bits, FP64 in memory).  Sampled states are returned
+ * in FP32.  sto_create_f64 selects an FP64 coupling instead (the precision
+ * of the paper's own benchmark, Sec. 3.3).
  *
  * Conventions for every entry point:
  *   - Return value: STO_OK (0) or a negative STO_E* code; sto_strerror()
@@ -113,13 +116,15 @@ typedef struct sto_info {
   int64_t N;
   int32_t grid;          /* CTAs, one per SM, co-resident */
   int32_t rows_max;      /* most oscillators owned by one CTA */
-  int32_t panel_cols;    /* columns of W per streamed panel */
+  int32_t panel_cols;    /* columns of W per streamed panel (128, or 64
+                            for sto_create_f64) */
   int32_t panels;        /* panels per row block (ceil(N / panel_cols)) */
   int32_t ring_slots;    /* shared-memory panel buffers per CTA */
   int32_t resident;      /* 1: each CTA keeps its rows of W on chip */
   int32_t smem_bytes;    /* dynamic shared memory per CTA */
   int32_t sm_count;      /* SMs of the device */
-  int64_t w_bytes;       /* bytes of W streamed per RK4 stage (4 N^2) */
+  int64_t w_bytes;       /* bytes of W streamed per RK4 stage (4 N^2, or
+                            8 N^2 for sto_create_f64) */
 } sto_info;
 
 typedef struct sto_handle sto_handle; /* opaque */
@@ -150,6 +155,36 @@ STO_API int sto_create(int64_t N, const sto_params* params, const float* W,
 STO_API int sto_create_ex(int64_t N, const sto_params* params, const float* W,
                   const float* w_in, const float* m0, void* stream,
                   const sto_config* cfg, sto_handle** out);
+
+/* Coupling products of sto_create_f64. */
+#define STO_PRODUCT_DF 1   /* W kept as an exact pair of floats (hi + lo, the
+                              FP64 value to 48 significand bits); products and
+                              row sums in double-float on the FP32 pipes */
+#define STO_PRODUCT_F64 2  /* W kept in FP64; FP64 fused multiply-adds */
+
+/* A reservoir with an FP64 coupling matrix: the paper's benchmark runs the
+ * whole method in FP64 (Sec. 3.3, Table 1: RK4 with dt = 1e-11 s, u = 0,
+ * random W with zero diagonal scaled to spectral radius 1), and this replica
+ * keeps W, the stage values exchanged between CTAs and the coupling sums
+ * at FP64 width instead of FP32.  8 N^2 bytes of W are read per RK4 stage.
+ *   N, params, w_in, stream, cfg, out   as for sto_create_ex (w_in and the
+ *               input series u of sto_run stay float32; both are exact in
+ *               FP64).
+ *   W           N x N row-major float64, host or device; copied.
+ *   m0          3 x N float64 initial state, host or device, or NULL for
+ *               Eq. (initial).
+ *   product     STO_PRODUCT_DF or STO_PRODUCT_F64 (see above).  The B300's
+ *               FP64 pipe is far slower than its FP32 pipes, so the
+ *               double-float product is the fast one; STO_PRODUCT_F64 gives
+ *               IEEE FP64 products and sums.
+ * sto_run, sto_run_group, sto_set_state[_f64], sto_get_state[_f64],
+ * sto_set_params, sto_get_info and sto_destroy work on the handle as on any
+ * other.  Largest N about 18000 with 148 CTAs (STO_ENOTSUP beyond).
+ * Errors: as sto_create_ex; STO_EINVAL for an unknown product;
+ *         sto_adjoint and sto_set_tableau on the handle return STO_ENOTSUP. */
+STO_API int sto_create_f64(int64_t N, const sto_params* params, const double* W,
+                           const float* w_in, const double* m0, void* stream,
+                           const sto_config* cfg, int32_t product, sto_handle** out);
 
 /* Replace the model parameters (not N, n_in or the plan).  Lets a caller
  * sweep I, A_cp, the gain, dt, substeps ... without re-uploading W.

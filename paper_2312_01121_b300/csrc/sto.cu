@@ -1,10 +1,12 @@
 // libsto host side: the C ABI declared in include/sto.h.
 //
 // The handle owns, in device memory of the device current at creation:
-//   W in the tiled layout of the plan (N x P*128 floats, zero padded),
-//   w_in (N x n_in floats), the FP64 state (3 x N doubles),
-//   the tagged m^x exchange buffer (2 x N 64-bit words), the error word,
-//   and staging buffers for calls made with host pointers.
+//   W in the tiled layout of the plan (N x P*128 floats, zero padded; P
+//   panels of 128 FP32 or, for the FP64 coupling modes, 64 eight-byte
+//   elements), w_in (N x n_in floats), the FP64 state (3 x N doubles),
+//   the tagged m^x exchange buffer (2 x N 64-bit words, twice that in the
+//   FP64 modes), the error word, and staging buffers for calls made with
+//   host pointers.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -56,37 +58,43 @@ struct Plan {
   size_t smem = 0;
 };
 
+// W elements per 512-byte panel row and bytes per element of a coupling mode.
+int panel_cols(int wmode) { return wmode == sto::kWf32 ? sto::kPanelCols : sto::kPanelCols / 2; }
+int w_elem_bytes(int wmode) { return wmode == sto::kWf32 ? 4 : 8; }
+
 // Dynamic shared memory of the stepper for a plan with `ns` ring slots.
-size_t smem_bytes(int R_max, int P, int ns) {
+size_t smem_bytes(int R_max, int P, int ns, int wmode = sto::kWf32) {
   size_t b = static_cast<size_t>(ns) * R_max * sto::kPanelCols * 4;  // ring
   b += static_cast<size_t>(P) * sto::kPanelCols * 4;                 // xs
-  b += static_cast<size_t>((R_max + 3) & ~3) * 4;                    // hs
+  b += static_cast<size_t>((R_max + 3) & ~3) * (wmode == sto::kWf32 ? 4 : 8);  // hs
   b += static_cast<size_t>(2 * ns) * 8 + 16;                         // barriers, abort flag
   return b;
 }
 
 // Choose the CTA count, panel ring and residency for N oscillators.
-int make_plan(int64_t N, int grid_req, int sm_count, size_t smem_max, Plan* out) {
+int make_plan(int64_t N, int grid_req, int sm_count, size_t smem_max, Plan* out,
+              int wmode = sto::kWf32) {
   Plan p;
-  p.P = static_cast<int>((N + sto::kPanelCols - 1) / sto::kPanelCols);
+  const int cols = panel_cols(wmode);
+  p.P = static_cast<int>((N + cols - 1) / cols);
   auto fill = [&](int G) -> bool {
     p.G = G;
     p.R_max = static_cast<int>((N + G - 1) / G);
     if (p.R_max > sto::kConsWarps * sto::kMaxRowsPerWarp) return false;
     p.rpw = (p.R_max + sto::kConsWarps - 1) / sto::kConsWarps;
-    if (smem_bytes(p.R_max, p.P, p.P) <= smem_max) {
+    if (smem_bytes(p.R_max, p.P, p.P, wmode) <= smem_max) {
       p.resident = 1;
       p.ns = p.P;
     } else {
       p.resident = 0;
-      const size_t fixed = smem_bytes(p.R_max, p.P, 0);
+      const size_t fixed = smem_bytes(p.R_max, p.P, 0, wmode);
       const size_t per = static_cast<size_t>(p.R_max) * sto::kPanelCols * 4 + 16;
       if (fixed >= smem_max) return false;
       p.ns = static_cast<int>((smem_max - fixed) / per);
       if (p.ns > 8) p.ns = 8;
       if (p.ns < 2) return false;
     }
-    p.smem = smem_bytes(p.R_max, p.P, p.ns);
+    p.smem = smem_bytes(p.R_max, p.P, p.ns, wmode);
     return p.smem <= smem_max;
   };
   if (grid_req > 0) {
@@ -162,6 +170,7 @@ struct sto_handle {
   double rk_a[16] = {};
   double rk_b[4] = {};
   int inject_cta = -1;
+  int wmode = sto::kWf32;      // coupling precision (sto_create_f64: kWdf or kWf64)
   uint64_t stage_counter = 0;
   float* d_W = nullptr;
   float* d_win = nullptr;
@@ -240,9 +249,9 @@ int raise_dyn_smem_cap(F* func) {
   return room;
 }
 
-template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward>
+template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward, int kW = sto::kWf32>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>);
+  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW>);
   if (room < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.G);
@@ -254,7 +263,7 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW>, a);
 }
 
 cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -283,12 +292,20 @@ cudaError_t launch_tableau(const Plan& pl, const sto::KArgs& a, cudaStream_t s) 
   return launch_rpw<16, false, B>(pl, a, s);
 }
 
-cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  if (pl.rpw <= 1) return launch_rpw<1>(pl, a, s);
-  if (pl.rpw <= 2) return launch_rpw<2>(pl, a, s);
-  if (pl.rpw <= 4) return launch_rpw<4>(pl, a, s);
-  if (pl.rpw <= 8) return launch_rpw<8>(pl, a, s);
-  return launch_rpw<16>(pl, a, s);
+template <int kW>
+cudaError_t launch_stepper_mode(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
+  constexpr int F = sto::kProgForward;
+  if (pl.rpw <= 1) return launch_rpw<1, false, F, kW>(pl, a, s);
+  if (pl.rpw <= 2) return launch_rpw<2, false, F, kW>(pl, a, s);
+  if (pl.rpw <= 4) return launch_rpw<4, false, F, kW>(pl, a, s);
+  if (pl.rpw <= 8) return launch_rpw<8, false, F, kW>(pl, a, s);
+  return launch_rpw<16, false, F, kW>(pl, a, s);
+}
+
+cudaError_t launch_stepper(const Plan& pl, const sto::KArgs& a, cudaStream_t s, int wmode = sto::kWf32) {
+  if (wmode == sto::kWdf) return launch_stepper_mode<sto::kWdf>(pl, a, s);
+  if (wmode == sto::kWf64) return launch_stepper_mode<sto::kWf64>(pl, a, s);
+  return launch_stepper_mode<sto::kWf32>(pl, a, s);
 }
 
 // Device copy of n floats from a host or device pointer into dst.
@@ -313,6 +330,21 @@ int any_nonfinite(const float* d_p, long long n, cudaStream_t s, int* d_flag, in
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     sto::nonfinite_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(d_p, n, d_flag);
+    STO_CUDA(cudaGetLastError());
+  }
+  STO_CUDA(cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  *result = (*h_flag != 0);
+  return STO_OK;
+}
+
+int any_nonfinite_f64(const double* d_p, long long n, cudaStream_t s, int* d_flag, int* h_flag,
+                      bool* result) {
+  STO_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  if (n > 0) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    sto::nonfinite_f64_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(d_p, n, d_flag);
     STO_CUDA(cudaGetLastError());
   }
   STO_CUDA(cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -347,14 +379,16 @@ int grow(float** buf, size_t* cap, size_t n) {
 // W of at most 96 MB (three quarters of the 126 MB L2) is streamed with an
 // evict_last hint so that it is re-read from L2 every stage; larger W is
 // streamed from HBM with evict_first so that it does not flush the rest.
-int l2_keeps(int64_t N) { return 4.0 * static_cast<double>(N) * N <= 96.0 * (1 << 20) ? 1 : 0; }
+int l2_keeps(int64_t N, int ebytes = 4) {
+  return static_cast<double>(ebytes) * static_cast<double>(N) * N <= 96.0 * (1 << 20) ? 1 : 0;
+}
 
 // Leading panels of every row block to keep L2-resident when W is larger
 // than L2: a `mb` megabyte slice of W (default 80 MB of the 126 MB L2).
-int keep_panels(int64_t N, int P, int mb) {
-  if (mb < 0 || l2_keeps(N)) return 0;
+int keep_panels(int64_t N, int P, int mb, int ebytes = 4) {
+  if (mb < 0 || l2_keeps(N, ebytes)) return 0;
   const double budget = (mb == 0 ? 80.0 : static_cast<double>(mb)) * (1 << 20);
-  const double wbytes = 4.0 * static_cast<double>(N) * N;
+  const double wbytes = static_cast<double>(ebytes) * static_cast<double>(N) * N;
   const int k = static_cast<int>(P * budget / wbytes);
   return k < P ? k : P;
 }
@@ -422,6 +456,12 @@ int grow_d(double** buf, size_t* cap, size_t n) {
   return STO_OK;
 }
 
+// Exchange buffer: two parity buffers of one tagged word per oscillator, or
+// of two in the FP64 modes.
+size_t xbuf_bytes(int64_t N, int wmode) {
+  return 2 * static_cast<size_t>(N) * 8 * (wmode == sto::kWf32 ? 1 : 2);
+}
+
 // Kernel arguments shared by the forward and adjoint launches of a handle.
 sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   const sto_params& P = h->params;
@@ -442,8 +482,8 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   a.comp = P.sample_component;
   a.inject_cta = h->inject_cta;
   a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
-  a.l2_keep = l2_keeps(h->N);
-  a.keep_panels = keep_panels(h->N, h->plan.P, h->l2_keep_mb);
+  a.l2_keep = l2_keeps(h->N, w_elem_bytes(h->wmode));
+  a.keep_panels = keep_panels(h->N, h->plan.P, h->l2_keep_mb, w_elem_bytes(h->wmode));
   set_constants(P, &a);
   a.rk_stages = h->rk_stages;
   for (int i = 0; i < 4; ++i) {
@@ -455,7 +495,7 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   const uint64_t stages = static_cast<uint64_t>(h->rk_stages) * static_cast<uint64_t>(P.substeps) *
                           static_cast<uint64_t>(T);
   if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
-    cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(h->N) * 8, h->stream);
+    cudaMemsetAsync(h->d_xbuf, 0xff, xbuf_bytes(h->N, h->wmode), h->stream);
     h->stage_counter = 0;
   }
   const uint64_t base = h->stage_counter + 1;
@@ -474,7 +514,7 @@ int engine_launch_on(sto_handle* h, cudaStream_t s, const float* d_u, int64_t T,
   a.rec_h = rec_h;
   STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
   if (h->rk_classic)
-    STO_CUDA(launch_stepper(h->plan, a, s));
+    STO_CUDA(launch_stepper(h->plan, a, s, h->wmode));
   else
     STO_CUDA(launch_tableau(h->plan, a, s));
   STO_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s));
@@ -532,6 +572,142 @@ int ensure_transpose(sto_handle* h) {
   return STO_OK;
 }
 
+// sto_create_ex and sto_create_f64: W is N x N float (wmode kWf32) or double
+// (the FP64 modes), m0 3 x N float or double (m0_f64) or NULL.
+int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, const float* w_in,
+                const void* m0, bool m0_f64, void* stream, const sto_config* cfg, sto_handle** out) {
+  if (!out) return STO_EINVAL;
+  *out = nullptr;
+  if (N < 1 || !W || !w_in) return STO_EINVAL;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (cfg) {
+    if (cfg->grid < 0 || cfg->timeout_ms < 0 || cfg->l2_keep_mb < -1) return STO_EINVAL;
+    for (int i = 0; i < 5; ++i)
+      if (cfg->reserved[i] != 0) return STO_EINVAL;
+  }
+  if (N > (1LL << 20)) return STO_ENOTSUP;
+
+  sto_handle* h = new (std::nothrow) sto_handle();
+  if (!h) return STO_ENOMEM;
+  h->N = N;
+  h->wmode = wmode;
+  h->params = *params;
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (cfg && cfg->timeout_ms > 0) h->timeout_ms = cfg->timeout_ms;
+  if (cfg) h->l2_keep_mb = cfg->l2_keep_mb;
+
+  auto fail = [&](int code) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  int smem_optin = 0;
+  if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
+          cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                  h->device)) != cudaSuccess)
+    return fail(cuda_fail(e));
+  rc = make_plan(N, cfg ? cfg->grid : 0, h->sm_count, static_cast<size_t>(smem_optin), &h->plan, wmode);
+  if (rc) return fail(rc);
+
+  const int n_in = params->n_in;
+  const size_t wt_elems = static_cast<size_t>(N) * h->plan.P * sto::kPanelCols;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  if (!alloc(reinterpret_cast<void**>(&h->d_W), wt_elems * 4) ||
+      !alloc(reinterpret_cast<void**>(&h->d_win), static_cast<size_t>(N) * n_in * 4) ||
+      !alloc(reinterpret_cast<void**>(&h->d_state), 3 * static_cast<size_t>(N) * 8) ||
+      !alloc(reinterpret_cast<void**>(&h->d_xbuf), xbuf_bytes(N, wmode)) ||
+      !alloc(reinterpret_cast<void**>(&h->d_err), 16))
+    return fail(STO_ENOMEM);
+  if (cudaMallocHost(reinterpret_cast<void**>(&h->h_err), 16) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_err = nullptr;
+    return fail(STO_ENOMEM);
+  }
+  cudaStream_t s = h->stream;
+
+  // W: stage row-major on the device, check, tile.
+  const size_t ebytes = static_cast<size_t>(w_elem_bytes(wmode));
+  const void* d_src = W;
+  void* d_tmp = nullptr;
+  if (!is_device_ptr(W)) {
+    if (!alloc(&d_tmp, static_cast<size_t>(N) * N * ebytes)) return fail(STO_ENOMEM);
+    e = cudaMemcpyAsync(d_tmp, W, static_cast<size_t>(N) * N * ebytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFree(d_tmp); return fail(cuda_fail(e)); }
+    d_src = d_tmp;
+  }
+  bool bad = false;
+  if (wmode == sto::kWf32)
+    rc = any_nonfinite(static_cast<const float*>(d_src), N * N, s, h->d_err, h->h_err, &bad);
+  else
+    rc = any_nonfinite_f64(static_cast<const double*>(d_src), N * N, s, h->d_err, h->h_err, &bad);
+  if (!rc && bad) rc = STO_ENONFINITE;
+  if (!rc) {
+    e = cudaMemsetAsync(h->d_W, 0, wt_elems * 4, s);
+    if (e == cudaSuccess) {
+      long long blocks = (N * N + 255) / 256;
+      if (blocks > 8192) blocks = 8192;
+      if (wmode == sto::kWf32)
+        sto::tile_w_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+            static_cast<const float*>(d_src), h->d_W, static_cast<int>(N), h->plan.G, h->plan.P);
+      else
+        sto::tile_w_wide_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+            static_cast<const double*>(d_src), h->d_W, static_cast<int>(N), h->plan.G, h->plan.P, wmode);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (d_tmp) cudaFree(d_tmp);
+  if (rc) return fail(rc);
+
+  // w_in
+  rc = upload_floats(h->d_win, w_in, static_cast<size_t>(N) * n_in, s);
+  if (!rc) {
+    rc = any_nonfinite(h->d_win, N * n_in, s, h->d_err, h->h_err, &bad);
+    if (!rc && bad) rc = STO_ENONFINITE;
+  }
+  if (rc) return fail(rc);
+
+  // exchange buffer: tag 0xffffffff is never used by a launch
+  e = cudaMemsetAsync(h->d_xbuf, 0xff, xbuf_bytes(N, wmode), s);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+
+  // state
+  std::vector<double> m(3 * static_cast<size_t>(N));
+  if (m0 && m0_f64) {
+    e = cudaMemcpyAsync(m.data(), m0, m.size() * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  } else if (m0) {
+    std::vector<float> mf;
+    rc = fetch_floats(&mf, static_cast<const float*>(m0), m.size(), s);
+    if (rc) return fail(rc);
+    for (size_t i = 0; i < m.size(); ++i) m[i] = mf[i];
+  } else {
+    const double phi0 = 2.0 * M_PI / 360.0;  // Eq. (initial)
+    for (int64_t k = 0; k < N; ++k) {
+      m[k] = std::sin(phi0) * std::cos(phi0);
+      m[N + k] = std::sin(phi0) * std::sin(phi0);
+      m[2 * N + k] = std::cos(phi0);
+    }
+  }
+  rc = set_state_host_f64(h, m.data());
+  if (rc) return fail(rc);
+  *out = h;
+  return STO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -570,124 +746,16 @@ int sto_create(int64_t N, const sto_params* params, const float* W, const float*
 
 int sto_create_ex(int64_t N, const sto_params* params, const float* W, const float* w_in,
                   const float* m0, void* stream, const sto_config* cfg, sto_handle** out) {
-  if (!out) return STO_EINVAL;
-  *out = nullptr;
-  if (N < 1 || !W || !w_in) return STO_EINVAL;
-  int rc = check_params(params);
-  if (rc) return rc;
-  if (cfg) {
-    if (cfg->grid < 0 || cfg->timeout_ms < 0 || cfg->l2_keep_mb < -1) return STO_EINVAL;
-    for (int i = 0; i < 5; ++i)
-      if (cfg->reserved[i] != 0) return STO_EINVAL;
-  }
-  if (N > (1LL << 20)) return STO_ENOTSUP;
+  return create_impl(N, params, W, sto::kWf32, w_in, m0, false, stream, cfg, out);
+}
 
-  sto_handle* h = new (std::nothrow) sto_handle();
-  if (!h) return STO_ENOMEM;
-  h->N = N;
-  h->params = *params;
-  h->stream = static_cast<cudaStream_t>(stream);
-  if (cfg && cfg->timeout_ms > 0) h->timeout_ms = cfg->timeout_ms;
-  if (cfg) h->l2_keep_mb = cfg->l2_keep_mb;
-
-  auto fail = [&](int code) {
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    free_handle(h);
-    return code;
-  };
-  cudaError_t e = cudaGetDevice(&h->device);
-  if (e != cudaSuccess) return fail(cuda_fail(e));
-  int smem_optin = 0;
-  if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
-          cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                  h->device)) != cudaSuccess)
-    return fail(cuda_fail(e));
-  rc = make_plan(N, cfg ? cfg->grid : 0, h->sm_count, static_cast<size_t>(smem_optin), &h->plan);
-  if (rc) return fail(rc);
-
-  const int n_in = params->n_in;
-  const size_t wt_elems = static_cast<size_t>(N) * h->plan.P * sto::kPanelCols;
-  auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
-      return false;
-    }
-    return true;
-  };
-  if (!alloc(reinterpret_cast<void**>(&h->d_W), wt_elems * 4) ||
-      !alloc(reinterpret_cast<void**>(&h->d_win), static_cast<size_t>(N) * n_in * 4) ||
-      !alloc(reinterpret_cast<void**>(&h->d_state), 3 * static_cast<size_t>(N) * 8) ||
-      !alloc(reinterpret_cast<void**>(&h->d_xbuf), 2 * static_cast<size_t>(N) * 8) ||
-      !alloc(reinterpret_cast<void**>(&h->d_err), 16))
-    return fail(STO_ENOMEM);
-  if (cudaMallocHost(reinterpret_cast<void**>(&h->h_err), 16) != cudaSuccess) {
-    cudaGetLastError();
-    h->h_err = nullptr;
-    return fail(STO_ENOMEM);
-  }
-  cudaStream_t s = h->stream;
-
-  // W: stage row-major on the device, check, tile.
-  const float* d_src = W;
-  float* d_tmp = nullptr;
-  if (!is_device_ptr(W)) {
-    if (!alloc(reinterpret_cast<void**>(&d_tmp), static_cast<size_t>(N) * N * 4))
-      return fail(STO_ENOMEM);
-    e = cudaMemcpyAsync(d_tmp, W, static_cast<size_t>(N) * N * 4, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) { cudaFree(d_tmp); return fail(cuda_fail(e)); }
-    d_src = d_tmp;
-  }
-  bool bad = false;
-  rc = any_nonfinite(d_src, N * N, s, h->d_err, h->h_err, &bad);
-  if (!rc && bad) rc = STO_ENONFINITE;
-  if (!rc) {
-    e = cudaMemsetAsync(h->d_W, 0, wt_elems * 4, s);
-    if (e == cudaSuccess) {
-      long long blocks = (N * N + 255) / 256;
-      if (blocks > 8192) blocks = 8192;
-      sto::tile_w_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-          d_src, h->d_W, static_cast<int>(N), h->plan.G, h->plan.P);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) rc = cuda_fail(e);
-  }
-  if (d_tmp) cudaFree(d_tmp);
-  if (rc) return fail(rc);
-
-  // w_in
-  rc = upload_floats(h->d_win, w_in, static_cast<size_t>(N) * n_in, s);
-  if (!rc) {
-    rc = any_nonfinite(h->d_win, N * n_in, s, h->d_err, h->h_err, &bad);
-    if (!rc && bad) rc = STO_ENONFINITE;
-  }
-  if (rc) return fail(rc);
-
-  // exchange buffer: tag 0xffffffff is never used by a launch
-  e = cudaMemsetAsync(h->d_xbuf, 0xff, 2 * static_cast<size_t>(N) * 8, s);
-  if (e != cudaSuccess) return fail(cuda_fail(e));
-
-  // state
-  std::vector<double> m(3 * static_cast<size_t>(N));
-  if (m0) {
-    std::vector<float> mf;
-    rc = fetch_floats(&mf, m0, m.size(), s);
-    if (rc) return fail(rc);
-    for (size_t i = 0; i < m.size(); ++i) m[i] = mf[i];
-  } else {
-    const double phi0 = 2.0 * M_PI / 360.0;  // Eq. (initial)
-    for (int64_t k = 0; k < N; ++k) {
-      m[k] = std::sin(phi0) * std::cos(phi0);
-      m[N + k] = std::sin(phi0) * std::sin(phi0);
-      m[2 * N + k] = std::cos(phi0);
-    }
-  }
-  rc = set_state_host_f64(h, m.data());
-  if (rc) return fail(rc);
-  *out = h;
-  return STO_OK;
+int sto_create_f64(int64_t N, const sto_params* params, const double* W, const float* w_in,
+                   const double* m0, void* stream, const sto_config* cfg, int32_t product,
+                   sto_handle** out) {
+  if (out) *out = nullptr;
+  if (product != STO_PRODUCT_DF && product != STO_PRODUCT_F64) return STO_EINVAL;
+  return create_impl(N, params, W, product == STO_PRODUCT_DF ? sto::kWdf : sto::kWf64, w_in, m0, true,
+                     stream, cfg, out);
 }
 
 void sto_destroy(sto_handle* h) {
@@ -711,13 +779,13 @@ int sto_get_info(const sto_handle* h, sto_info* out) {
   out->N = h->N;
   out->grid = h->plan.G;
   out->rows_max = h->plan.R_max;
-  out->panel_cols = sto::kPanelCols;
+  out->panel_cols = panel_cols(h->wmode);
   out->panels = h->plan.P;
   out->ring_slots = h->plan.ns;
   out->resident = h->plan.resident;
   out->smem_bytes = static_cast<int32_t>(h->plan.smem);
   out->sm_count = h->sm_count;
-  out->w_bytes = 4 * h->N * h->N;
+  out->w_bytes = w_elem_bytes(h->wmode) * h->N * h->N;
   return STO_OK;
 }
 
@@ -805,6 +873,7 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
                 int32_t ckpt_every, sto_grads* out) {
   if (!h || T < 1 || !u || !dL_dstates || !out || ckpt_every < 1) return STO_EINVAL;
   if (!h->rk_classic) return STO_ENOTSUP;  // the adjoint is that of classic RK4
+  if (h->wmode != sto::kWf32) return STO_ENOTSUP;  // and of the FP32 coupling
   const sto_params& P = h->params;
   const uint64_t stages = 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T);
   if (T > (1LL << 31) - 1 || stages > 0x40000000ULL) return STO_ENOTSUP;
@@ -986,6 +1055,7 @@ int sto_set_tableau(sto_handle* h, int32_t stages, const double* a, const double
     return STO_OK;
   }
   if (stages < 1 || stages > 4 || !a || !b) return STO_EINVAL;
+  if (h->wmode != sto::kWf32) return STO_ENOTSUP;  // tableaus run with the FP32 coupling
   for (int i = 0; i < stages; ++i) {
     if (!std::isfinite(b[i])) return STO_EINVAL;
     for (int j = 0; j < stages; ++j) {

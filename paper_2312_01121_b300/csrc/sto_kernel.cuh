@@ -21,6 +21,18 @@
 // has read every tag-g word, which every owner wrote after reading all of
 // its tag g - 1 words.
 //
+// Coupling precision (template parameter kW).  kWf32: W and the product in
+// FP32 (the words above).  The two FP64 modes replicate the paper's own FP64
+// benchmark (Sec. 3.3): the published value is the full double-float stage
+// value, two tagged words per oscillator (low 32 bits of each word: hi and lo
+// floats for kWdf, low and high halves of the FP64 value for kWf64) at
+// xbuf[(g & 1) * 2N + 2k + {0, 1}]; a reader takes the pair once both words
+// carry tag g.  kWdf stores W as an exact pair of floats per element (FP64
+// rounded to 48 significand bits) and forms the products and row sums in
+// double-float on the FP32 pipes; kWf64 stores W in FP64 and uses FP64 fused
+// multiply-adds.  A W row panel is 512 bytes in every mode (128 FP32 or 64
+// wide elements), so the producer and the ring are the same.
+//
 // Every wait is bounded by a_.timeout_ns of %globaltimer; on expiry the kernel
 // records STO_ETIMEOUT in the error word; the consumer warps of a CTA agree
 // on leaving through an OR-reducing barrier (bar.red.or), and the producer
@@ -81,6 +93,7 @@ struct KArgs {
 };
 
 enum ProgramKind { kProgForward = 0, kProgAdjoint = 1, kProgTableau = 2 };
+enum CouplingMode { kWf32 = 0, kWdf = 1, kWf64 = 2 };
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -250,6 +263,36 @@ __device__ __forceinline__ bool gather_x(const KArgs& a, float* xs, unsigned tag
   return true;
 }
 
+// The FP64 modes: the pair of tagged words of every oscillator, stored as
+// two 32-bit halves in xs2 (hi, lo floats or the FP64 value's bits).
+__device__ __forceinline__ bool gather_x2(const KArgs& a, uint2* xs2, unsigned tag, int g, int ng) {
+  const unsigned long long* xb = a.xbuf + static_cast<size_t>(tag & 1u) * 2 * a.N;
+  for (int base = g; base < a.N; base += 2 * ng) {
+    unsigned long long w[4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = base + q * ng;
+      w[2 * q] = (i < a.N) ? ld_relaxed_u64(xb + 2 * static_cast<size_t>(i)) : 0ull;
+      w[2 * q + 1] = (i < a.N) ? ld_relaxed_u64(xb + 2 * static_cast<size_t>(i) + 1) : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = base + q * ng;
+      if (i < a.N) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (static_cast<unsigned>(w[2 * q + h] >> 32) != tag) {
+            w[2 * q + h] = poll_word(xb + 2 * static_cast<size_t>(i) + h, tag, a.err, a.timeout_ns);
+            if (w[2 * q + h] == 0ull) return false;
+          }
+        }
+        xs2[i] = make_uint2(static_cast<unsigned>(w[2 * q]), static_cast<unsigned>(w[2 * q + 1]));
+      }
+    }
+  }
+  return true;
+}
+
 // Eq. (gov) is affine in the x-field that coupling and input add to b:
 // with b = b0 + h e_x,
 //   dt dm/dt = -gamma' dt [m x b + alpha m x (m x b)] = A(m) + h B(m),
@@ -288,20 +331,47 @@ __device__ __forceinline__ void llg_affine(const KArgs& a, const df m[3], df A[3
 // W z for the published z.  What an oscillator's owner thread does with the
 // reduced sum, and what it publishes next, is its "program".
 
-// Publishes oscillator `node`'s stage value under tag `tg`.
+// Publishes oscillator `node`'s stage value under tag `tg`: its FP32
+// rounding (kWf32), or the full double-float value (kWdf as two floats,
+// kWf64 as an FP64 value).
 struct Publisher {
   unsigned long long* xbuf;
   float* xs;
   int N;
+  int mode;      // CouplingMode of the launch
   bool single;   // one CTA: write shared memory directly
   bool enabled;  // false only for the CTA a test stalls on purpose
-  __device__ __forceinline__ void operator()(int node, float v, unsigned tg) const {
-    if (single)
-      xs[node] = v;
-    else if (enabled)
-      st_relaxed_u64(xbuf + static_cast<size_t>(tg & 1u) * N + node, pack_x(v, tg));
+  __device__ __forceinline__ void operator()(int node, df v, unsigned tg) const {
+    if (mode == kWf32) {
+      if (single)
+        xs[node] = v.hi;
+      else if (enabled)
+        st_relaxed_u64(xbuf + static_cast<size_t>(tg & 1u) * N + node, pack_x(v.hi, tg));
+      return;
+    }
+    uint32_t w0, w1;
+    if (mode == kWdf) {
+      w0 = __float_as_uint(v.hi);
+      w1 = __float_as_uint(v.lo);
+    } else {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(df_to_double(v)));
+      w0 = static_cast<uint32_t>(b);
+      w1 = static_cast<uint32_t>(b >> 32);
+    }
+    if (single) {
+      reinterpret_cast<uint2*>(xs)[node] = make_uint2(w0, w1);
+    } else if (enabled) {
+      unsigned long long* p = xbuf + static_cast<size_t>(tg & 1u) * 2 * N + 2 * static_cast<size_t>(node);
+      const unsigned long long t = static_cast<unsigned long long>(tg) << 32;
+      st_relaxed_u64(p, t | w0);
+      st_relaxed_u64(p + 1, t | w1);
+    }
   }
 };
+
+// A_cp times the reduced coupling sum, as a double-float field.
+__device__ __forceinline__ df acp_times(const KArgs& a, float h) { return df_mul_f(a.acp, h); }
+__device__ __forceinline__ df acp_times(const KArgs& a, df h) { return df_mul(a.acp, h); }
 
 // Forward RK4 (Sec. 3.2) of Eq. (gov): publishes m^x of every stage state.
 struct ForwardProgram {
@@ -326,24 +396,28 @@ struct ForwardProgram {
     t = 0;
     sub = 0;
     load_hin(a, node);
-    pub(node, ms[0].hi, tag);
+    pub(node, ms[0], tag);
     llg_affine(a, ms, fa, fb);
   }
 
-  // Finish stage g with the raw coupling sum hraw = (W x)_node, then
-  // publish the next stage's m^x under next_tag.
-  __device__ __forceinline__ void stage(const KArgs& a, int node, long long g, float hraw,
+  // Finish stage g with the raw coupling sum hraw = (W x)_node (a float, or
+  // a double-float in the FP64 modes), then publish the next stage's m^x
+  // under next_tag.
+  template <class HS>
+  __device__ __forceinline__ void stage(const KArgs& a, int node, long long g, HS hraw,
                                         const Publisher& pub, unsigned next_tag) {
     const int st = static_cast<int>(g & 3);
-    if (a.rec_h) {
-      const size_t n = static_cast<size_t>(g >> 2);
-      a.rec_h[(n * 4 + st) * a.N + node] = hraw;
-      if (st == 0) {
+    if constexpr (std::is_same<HS, float>::value) {  // recording (FP32 coupling only)
+      if (a.rec_h) {
+        const size_t n = static_cast<size_t>(g >> 2);
+        a.rec_h[(n * 4 + st) * a.N + node] = hraw;
+        if (st == 0) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) a.rec_m[(n * 3 + i) * a.N + node] = make_float2(mn[i].hi, mn[i].lo);
+          for (int i = 0; i < 3; ++i) a.rec_m[(n * 3 + i) * a.N + node] = make_float2(mn[i].hi, mn[i].lo);
+        }
       }
     }
-    const df hx = df_add(df_mul_f(a.acp, hraw), hin);
+    const df hx = df_add(acp_times(a, hraw), hin);
     df d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = df_fma(hx, fb[i], fa[i]);
@@ -372,7 +446,7 @@ struct ForwardProgram {
       }
       if (++t < a.T) load_hin(a, node);
     }
-    pub(node, ms[0].hi, next_tag);
+    pub(node, ms[0], next_tag);
     llg_affine(a, ms, fa, fb);  // for the next stage, overlapping the exchange
   }
 
@@ -408,13 +482,14 @@ struct TableauProgram {
     }
     t = sub = st = 0;
     load_hin(a, node);
-    pub(node, ms[0].hi, tag);
+    pub(node, ms[0], tag);
     llg_affine(a, ms, fa, fb);
   }
 
-  __device__ __forceinline__ void stage(const KArgs& a, int node, long long /*g*/, float hraw,
+  template <class HS>
+  __device__ __forceinline__ void stage(const KArgs& a, int node, long long /*g*/, HS hraw,
                                         const Publisher& pub, unsigned next_tag) {
-    const df hx = df_add(df_mul_f(a.acp, hraw), hin);
+    const df hx = df_add(acp_times(a, hraw), hin);
     df d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -451,7 +526,7 @@ struct TableauProgram {
         if (++t < a.T) load_hin(a, node);
       }
     }
-    pub(node, ms[0].hi, next_tag);
+    pub(node, ms[0], next_tag);
     llg_affine(a, ms, fa, fb);
   }
 
@@ -598,7 +673,7 @@ struct AdjointProgram {
   __device__ __forceinline__ void publish_stage(const KArgs& a, int node, int q, const df v[3],
                                                 const Publisher& pub, unsigned tag) {
     const df gb = gbar_of(a, q, v);
-    pub(node, gb.hi, tag);
+    pub(node, gb, tag);
     local_vjp(a, q, v, gb);  // overlaps the exchange
   }
 
@@ -659,11 +734,151 @@ struct AdjointProgram {
 
 // ------------------------------------------------------------ the stepper
 
+// Per-row partial sums of W x for the rows a consumer warp owns (rows warp,
+// warp + 15, ...), one specialisation per coupling mode.  panel() adds one
+// 512-byte panel row per owned row; store() reduces across the warp and
+// writes the row sums to shared memory (float, float2 hi/lo, or double).
+template <int kW, int RPW>
+struct RowSums;
+
+template <int RPW>
+struct RowSums<kWf32, RPW> {
+  float s[RPW];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) s[q] = 0.f;
+  }
+  __device__ __forceinline__ void panel(const float* slot, const float* xs, int j, int warp, int lane, int R) {
+    const float4* p4 = reinterpret_cast<const float4*>(slot);
+    const float4 xv = reinterpret_cast<const float4*>(xs)[j * (kPanelCols / 4) + lane];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int r = warp + q * kConsWarps;
+      if (r < R) {
+        const float4 w = p4[r * (kPanelCols / 4) + lane];
+        float v = s[q];
+        v = fmaf(w.x, xv.x, v);
+        v = fmaf(w.y, xv.y, v);
+        v = fmaf(w.z, xv.z, v);
+        v = fmaf(w.w, xv.w, v);
+        s[q] = v;
+      }
+    }
+  }
+  __device__ __forceinline__ void store(float* hs, int warp, int lane, int R) {
+    // butterfly sums of all rows at once (rows past R hold 0), so the
+    // shuffle chains of different rows overlap
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * kConsWarps;
+        if (r < R) hs[r] = s[q];
+      }
+    }
+  }
+};
+
+// Double-float: per element (wh + wl)(xh + xl) = p + e with p = fl(wh xh)
+// and e = its exact error + wh xl + wl xh (wl xl, below 2^-48 relative, is
+// dropped); p enters the running sum through Knuth's TwoSum, e and the sum's
+// rounding errors collect in the lo word.
+template <int RPW>
+struct RowSums<kWdf, RPW> {
+  float hi[RPW], lo[RPW];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) hi[q] = lo[q] = 0.f;
+  }
+  __device__ __forceinline__ static void acc(float& sh, float& sl, float wh, float wl, float xh, float xl) {
+    const float p = __fmul_rn(wh, xh);
+    float e = __fmaf_rn(wh, xh, -p);
+    e = __fmaf_rn(wh, xl, e);
+    e = __fmaf_rn(wl, xh, e);
+    const df t = two_sum(sh, p);
+    sh = t.hi;
+    sl = __fadd_rn(sl, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ void panel(const float* slot, const float* xs, int j, int warp, int lane, int R) {
+    const float4* p4 = reinterpret_cast<const float4*>(slot);
+    // (xh, xl) of elements 64 j + 2 lane and 64 j + 2 lane + 1
+    const float4 xv = reinterpret_cast<const float4*>(xs)[j * (kPanelCols / 4) + lane];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int r = warp + q * kConsWarps;
+      if (r < R) {
+        const float4 w = p4[r * (kPanelCols / 4) + lane];
+        acc(hi[q], lo[q], w.x, w.y, xv.x, xv.y);
+        acc(hi[q], lo[q], w.z, w.w, xv.z, xv.w);
+      }
+    }
+  }
+  __device__ __forceinline__ void store(float* hs, int warp, int lane, int R) {
+    df v[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) v[q] = two_sum(hi[q], lo[q]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const df o{__shfl_xor_sync(0xffffffffu, v[q].hi, off), __shfl_xor_sync(0xffffffffu, v[q].lo, off)};
+        v[q] = df_add(v[q], o);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * kConsWarps;
+        if (r < R) reinterpret_cast<float2*>(hs)[r] = make_float2(v[q].hi, v[q].lo);
+      }
+    }
+  }
+};
+
+template <int RPW>
+struct RowSums<kWf64, RPW> {
+  double s[RPW];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) s[q] = 0.0;
+  }
+  __device__ __forceinline__ void panel(const float* slot, const float* xs, int j, int warp, int lane, int R) {
+    const double2* p2 = reinterpret_cast<const double2*>(slot);
+    const double2 xv = reinterpret_cast<const double2*>(xs)[j * (kPanelCols / 4) + lane];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int r = warp + q * kConsWarps;
+      if (r < R) {
+        const double2 w = p2[r * (kPanelCols / 4) + lane];
+        s[q] = fma(w.y, xv.y, fma(w.x, xv.x, s[q]));
+      }
+    }
+  }
+  __device__ __forceinline__ void store(float* hs, int warp, int lane, int R) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int r = warp + q * kConsWarps;
+        if (r < R) reinterpret_cast<double*>(hs)[r] = s[q];
+      }
+    }
+  }
+};
+
 // kRowMajorW = false: a.W is the tiled copy made by sto_create (one bulk copy
 // per panel).  kRowMajorW = true: a.W is the caller's row-major N x N matrix
 // (N a multiple of 4); each panel arrives as one bulk copy per row, issued by
 // the 32 lanes of the producer warp.  Consumers are identical in both.
-template <int RPW, bool kRowMajorW, int kProg = kProgForward>
+template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int c = blockIdx.x;
@@ -677,7 +892,9 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   float* ring = reinterpret_cast<float*>(smem);
   float* xs = ring + slot_floats * a.ns;
   float* hs = xs + static_cast<size_t>(a.P) * kPanelCols;
-  uint64_t* full = reinterpret_cast<uint64_t*>(hs + ((R_max + 3) & ~3));
+  // row sums: one float per row, two in the FP64 modes (8-byte aligned:
+  // every region before them is a multiple of 512 bytes)
+  uint64_t* full = reinterpret_cast<uint64_t*>(hs + (kW == kWf32 ? 1 : 2) * ((R_max + 3) & ~3));
   uint64_t* empty = full + a.ns;
   volatile int* s_abort = reinterpret_cast<volatile int*>(empty + a.ns);
 
@@ -807,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   const int ctid = tid;
   const int node = r0 + ctid;
   const bool owner = ctid < R;
-  const Publisher pub{a.xbuf, xs, a.N, G == 1, c != a.inject_cta};
+  const Publisher pub{a.xbuf, xs, a.N, kW, G == 1, c != a.inject_cta};
   // owners sit in the first warps; the others gather while owners work
   const int owner_warps = (R_max + 31) / 32;
   const int gather_first = owner_warps < kConsWarps ? owner_warps * 32 : 0;
@@ -837,60 +1054,70 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   for (long long g = 0; g < n_stages && !aborted; ++g) {
     // 1. the stage's published value of every oscillator
     bool fail = false;
-    if (G > 1 && ctid >= gather_first &&
-        !gather_x(a, xs, tag, ctid - gather_first, kCons - gather_first)) {
-      fail = true;
-      *s_abort = 1;
+    if (G > 1 && ctid >= gather_first) {
+      bool got;
+      if constexpr (kW == kWf32)
+        got = gather_x(a, xs, tag, ctid - gather_first, kCons - gather_first);
+      else
+        got = gather_x2(a, reinterpret_cast<uint2*>(xs), tag, ctid - gather_first, kCons - gather_first);
+      if (!got) {
+        fail = true;
+        *s_abort = 1;
+      }
     }
     if (consumer_sync_or(fail)) { aborted = true; break; }
     // 2. h = W x over this CTA's rows, panel by panel
-    float acc[RPW];
-#pragma unroll
-    for (int qq = 0; qq < RPW; ++qq) acc[qq] = 0.f;
-    const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
+    RowSums<kW, RPW> sums;
+    sums.zero();
     if (a.resident) {
-      // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
-      // with few rows per warp, four partial sums per row shorten the
-      // dependent FMA chain
-      constexpr int kPart = RPW <= 2 ? 4 : 1;
-      float part[RPW][kPart];
+      if constexpr (kW == kWf32) {
+        // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
+        // with few rows per warp, four partial sums per row shorten the
+        // dependent FMA chain
+        const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
+        constexpr int kPart = RPW <= 2 ? 4 : 1;
+        float part[RPW][kPart];
 #pragma unroll
-      for (int qq = 0; qq < RPW; ++qq)
+        for (int qq = 0; qq < RPW; ++qq)
 #pragma unroll
-        for (int k = 0; k < kPart; ++k) part[qq][k] = 0.f;
-      const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
-      const int pstride = static_cast<int>(slot_floats / 4);
+          for (int k = 0; k < kPart; ++k) part[qq][k] = 0.f;
+        const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
+        const int pstride = static_cast<int>(slot_floats / 4);
 #pragma unroll 4
-      for (int j = 0; j < a.P; ++j) {
-        const float4 xv = x4[j * (kPanelCols / 4)];
-        const float4* pj = w4 + j * pstride;
+        for (int j = 0; j < a.P; ++j) {
+          const float4 xv = x4[j * (kPanelCols / 4)];
+          const float4* pj = w4 + j * pstride;
 #pragma unroll
-        for (int qq = 0; qq < RPW; ++qq) {
-          const int r = warp + qq * kConsWarps;
-          if (r < R) {
-            const float4 w = pj[r * (kPanelCols / 4)];
-            if constexpr (kPart == 4) {
-              part[qq][0] = fmaf(w.x, xv.x, part[qq][0]);
-              part[qq][1] = fmaf(w.y, xv.y, part[qq][1]);
-              part[qq][2] = fmaf(w.z, xv.z, part[qq][2]);
-              part[qq][3] = fmaf(w.w, xv.w, part[qq][3]);
-            } else {
-              float v = part[qq][0];
-              v = fmaf(w.x, xv.x, v);
-              v = fmaf(w.y, xv.y, v);
-              v = fmaf(w.z, xv.z, v);
-              v = fmaf(w.w, xv.w, v);
-              part[qq][0] = v;
+          for (int qq = 0; qq < RPW; ++qq) {
+            const int r = warp + qq * kConsWarps;
+            if (r < R) {
+              const float4 w = pj[r * (kPanelCols / 4)];
+              if constexpr (kPart == 4) {
+                part[qq][0] = fmaf(w.x, xv.x, part[qq][0]);
+                part[qq][1] = fmaf(w.y, xv.y, part[qq][1]);
+                part[qq][2] = fmaf(w.z, xv.z, part[qq][2]);
+                part[qq][3] = fmaf(w.w, xv.w, part[qq][3]);
+              } else {
+                float v = part[qq][0];
+                v = fmaf(w.x, xv.x, v);
+                v = fmaf(w.y, xv.y, v);
+                v = fmaf(w.z, xv.z, v);
+                v = fmaf(w.w, xv.w, v);
+                part[qq][0] = v;
+              }
             }
           }
         }
-      }
 #pragma unroll
-      for (int qq = 0; qq < RPW; ++qq) {
-        if constexpr (kPart == 4)
-          acc[qq] = (part[qq][0] + part[qq][1]) + (part[qq][2] + part[qq][3]);
-        else
-          acc[qq] = part[qq][0];
+        for (int qq = 0; qq < RPW; ++qq) {
+          if constexpr (kPart == 4)
+            sums.s[qq] = (part[qq][0] + part[qq][1]) + (part[qq][2] + part[qq][3]);
+          else
+            sums.s[qq] = part[qq][0];
+        }
+      } else {
+#pragma unroll 2
+        for (int j = 0; j < a.P; ++j) sums.panel(ring + static_cast<size_t>(j) * slot_floats, xs, j, warp, lane, R);
       }
     } else {
       for (int j = 0; j < a.P; ++j) {
@@ -905,21 +1132,7 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
           fail = true;
           break;
         }
-        const float4* p4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * slot_floats);
-        const float4 xv = x4[j * (kPanelCols / 4)];
-#pragma unroll
-        for (int qq = 0; qq < RPW; ++qq) {
-          const int r = warp + qq * kConsWarps;
-          if (r < R) {
-            const float4 w = p4[r * (kPanelCols / 4) + lane];
-            float v = acc[qq];
-            v = fmaf(w.x, xv.x, v);
-            v = fmaf(w.y, xv.y, v);
-            v = fmaf(w.z, xv.z, v);
-            v = fmaf(w.w, xv.w, v);
-            acc[qq] = v;
-          }
-        }
+        sums.panel(ring + static_cast<size_t>(slot) * slot_floats, xs, j, warp, lane, R);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         if (++cslot == a.ns) {
@@ -928,24 +1141,20 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
         }
       }
     }
-    // butterfly sums of all rows at once (rows past R hold 0), so the
-    // shuffle chains of different rows overlap
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-      for (int qq = 0; qq < RPW; ++qq) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], off);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int qq = 0; qq < RPW; ++qq) {
-        const int r = warp + qq * kConsWarps;
-        if (r < R) hs[r] = acc[qq];
-      }
-    }
+    sums.store(hs, warp, lane, R);
     if (consumer_sync_or(fail)) { aborted = true; break; }
 
     // 3. the owner's program finishes the stage and publishes the next
-    if (owner) prog.stage(a, node, g, hs[ctid], pub, tag + 1u);
+    if (owner) {
+      if constexpr (kW == kWf32) {
+        prog.stage(a, node, g, hs[ctid], pub, tag + 1u);
+      } else if constexpr (kW == kWdf) {
+        const float2 v = reinterpret_cast<const float2*>(hs)[ctid];
+        prog.stage(a, node, g, df{v.x, v.y}, pub, tag + 1u);
+      } else {
+        prog.stage(a, node, g, df_from_double(reinterpret_cast<const double*>(hs)[ctid]), pub, tag + 1u);
+      }
+    }
     ++tag;
   }
   if (!aborted && owner) prog.finish(a, node);
@@ -975,6 +1184,40 @@ __global__ void tile_w_kernel(const float* __restrict__ W, float* __restrict__ W
     const int r = k - r0, j = i / kPanelCols, col = i % kPanelCols;
     Wt[static_cast<size_t>(r0) * P * kPanelCols + static_cast<size_t>(j) * R * kPanelCols +
        static_cast<size_t>(r) * kPanelCols + col] = W[idx];
+  }
+}
+
+// The FP64 modes: a row-major N x N FP64 matrix into the same tiled layout
+// with 64 elements (512 bytes) per panel row; element (k, i) takes the two
+// floats at row offset 2 (i mod 64): its hi/lo split (kWdf: hi = fl32(w),
+// lo = fl32(w - hi), so hi + lo is w to 48 significand bits) or the FP64
+// value itself (kWf64).  The destination must be zeroed beforehand.
+__global__ void tile_w_wide_kernel(const double* __restrict__ W, float* __restrict__ Wt, int N, int G,
+                                   int P, int mode) {
+  constexpr int kCols = kPanelCols / 2;
+  const int q = N / G, rem = N % G;
+  const long long total = static_cast<long long>(N) * N;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(idx / N), i = static_cast<int>(idx % N);
+    int r0, R;
+    if (k < rem * (q + 1)) {
+      r0 = (k / (q + 1)) * (q + 1);
+      R = q + 1;
+    } else {
+      r0 = ((k - rem * (q + 1)) / q) * q + rem * (q + 1);
+      R = q;
+    }
+    const int r = k - r0, j = i / kCols, col = i % kCols;
+    float* dst = Wt + static_cast<size_t>(r0) * P * kPanelCols + static_cast<size_t>(j) * R * kPanelCols +
+                 static_cast<size_t>(r) * kPanelCols + 2 * col;
+    const double w = W[idx];
+    if (mode == kWdf) {
+      const float hi = __double2float_rn(w);
+      reinterpret_cast<float2*>(dst)[0] = make_float2(hi, __double2float_rn(w - static_cast<double>(hi)));
+    } else {
+      reinterpret_cast<double*>(dst)[0] = w;
+    }
   }
 }
 
@@ -1012,6 +1255,14 @@ __global__ void transpose_tiled_kernel(const float* __restrict__ Wt, float* __re
 
 // flag = 1 if any of the n floats is NaN or Inf.
 __global__ void nonfinite_kernel(const float* __restrict__ p, long long n, int* flag) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (!isfinite(p[i])) *flag = 1;
+  }
+}
+
+// flag = 1 if any of the n doubles is NaN or Inf.
+__global__ void nonfinite_f64_kernel(const double* __restrict__ p, long long n, int* flag) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     if (!isfinite(p[i])) *flag = 1;

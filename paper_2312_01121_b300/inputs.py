@@ -44,6 +44,19 @@ def coupling_paper(N: int, seed: int = 0) -> np.ndarray:
     return W
 
 
+def coupling_paper_circular(N: int, seed: int = 0) -> np.ndarray:
+    """The paper's structure (zero diagonal, U[-1,1] off-diagonal) scaled by
+    the circular law's spectral radius sqrt(N/3) instead of an eigensolve
+    (which takes minutes at N = 10^4); for timing runs, where the radius
+    only needs to be about 1.  Same random draws as coupling_paper."""
+    g = rng(seed, STREAM_W)
+    W = g.uniform(-1.0, 1.0, size=(N, N))
+    np.fill_diagonal(W, 0.0)
+    if N > 1:
+        W /= np.sqrt(N / 3.0)
+    return W
+
+
 def coupling_gaussian(N: int, seed: int = 0, std: float | None = None,
                       dtype=np.float64) -> np.ndarray:
     """N x N: zero diagonal, i.i.d. normal entries of std 0.1/sqrt(N)."""

@@ -22,6 +22,9 @@ LIB_PATH = os.path.join(_PKG, "libsto.so")
 STO_OK, STO_EINVAL, STO_ENOMEM, STO_ECUDA, STO_ETIMEOUT, STO_ENONFINITE, STO_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6)
 STO_ETOOBIG = -7
+STO_PRODUCT_DF, STO_PRODUCT_F64 = 1, 2
+# coupling precision of a Reservoir -> product of sto_create_f64 (None: FP32 sto_create)
+COUPLINGS = {"f32": None, "df64": STO_PRODUCT_DF, "f64": STO_PRODUCT_F64}
 
 
 class StoError(RuntimeError):
@@ -81,6 +84,8 @@ SIGNATURES = {
                                   ctypes.POINTER(_VP)]),
     "sto_create_ex": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
                                      ctypes.POINTER(sto_config), ctypes.POINTER(_VP)]),
+    "sto_create_f64": (ctypes.c_int, [_I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
+                                      ctypes.POINTER(sto_config), _I32, ctypes.POINTER(_VP)]),
     "sto_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(sto_params)]),
     "sto_set_state": (ctypes.c_int, [_VP, _VP]),
     "sto_get_state": (ctypes.c_int, [_VP, _VP]),
@@ -221,6 +226,24 @@ def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout
     return h.value
 
 
+def sto_create_f64(N, params: Params, W, w_in, m0=None, stream=None, product=STO_PRODUCT_DF,
+                   grid=0, timeout_ms=0, l2_keep_mb=0):
+    """Handle with an FP64 coupling (the paper's benchmark precision).  W and
+    m0: float64 (numpy or torch); w_in: float32.  product: STO_PRODUCT_DF
+    (double-float on the FP32 pipes) or STO_PRODUCT_F64 (FP64 FMA)."""
+    lib = load_library()
+    pW, kW = _ptr(W, np.float64)
+    pwin, kwin = _ptr(w_in, np.float32)
+    pm0, km0 = _ptr(m0, np.float64)
+    h = _VP()
+    cp = params.to_c()
+    cfg = sto_config(grid=grid, timeout_ms=timeout_ms, l2_keep_mb=l2_keep_mb)
+    _check(lib.sto_create_f64(N, ctypes.byref(cp), pW, pwin, pm0, _stream_ptr(stream),
+                              ctypes.byref(cfg), int(product), ctypes.byref(h)))
+    del kW, kwin, km0
+    return h.value
+
+
 def sto_run(h, u, T, states_out=None):
     pu, ku = _ptr(u, np.float32)
     if states_out is not None and not hasattr(states_out, "data_ptr"):
@@ -333,14 +356,26 @@ def sto_strerror(code: int) -> str:
 
 
 class Reservoir:
-    """One reservoir of N coupled STOs on the current CUDA device."""
+    """One reservoir of N coupled STOs on the current CUDA device.
+
+    coupling: "f32" (FP32 W and products, W and m0 float32), or the FP64
+    coupling of the paper's benchmark, "df64" (double-float products) or
+    "f64" (FP64 FMA), with W and m0 float64."""
 
     def __init__(self, W, w_in, params: Params | None = None, m0=None, stream=None,
-                 grid: int = 0, timeout_ms: int = 0, l2_keep_mb: int = 0):
+                 grid: int = 0, timeout_ms: int = 0, l2_keep_mb: int = 0, coupling: str = "f32"):
         self.params = params or Params()
         self.N = int(W.shape[0])
-        self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms,
-                                 l2_keep_mb)
+        self.handle = None
+        if coupling not in COUPLINGS:
+            raise ValueError(f"coupling must be one of {sorted(COUPLINGS)}")
+        self.coupling = coupling
+        if COUPLINGS[coupling] is None:
+            self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms,
+                                     l2_keep_mb)
+        else:
+            self.handle = sto_create_f64(self.N, self.params, W, w_in, m0, stream, COUPLINGS[coupling],
+                                         grid, timeout_ms, l2_keep_mb)
 
     def run(self, u, states_out=None, T=None):
         """Advance over T = len(u) input samples; fills states_out (T x N) if given."""

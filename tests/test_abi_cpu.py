@@ -98,6 +98,17 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.sto_create(2, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
     bad = sto.Params(sample_component=3).to_c()
     assert lib.sto_create(2, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    dbuf = (ctypes.c_double * 4)()
+    for product in (0, 3, -1):
+        assert lib.sto_create_f64(2, ctypes.byref(cp), dbuf, buf, None, None, None, product,
+                                  ctypes.byref(h)) == sto.STO_EINVAL
+    for product in (sto.STO_PRODUCT_DF, sto.STO_PRODUCT_F64):
+        assert lib.sto_create_f64(0, ctypes.byref(cp), dbuf, buf, None, None, None, product,
+                                  ctypes.byref(h)) == sto.STO_EINVAL
+        assert lib.sto_create_f64(2, ctypes.byref(cp), None, buf, None, None, None, product,
+                                  ctypes.byref(h)) == sto.STO_EINVAL
+        assert lib.sto_create_f64(2, ctypes.byref(cp), dbuf, buf, None, None, None, product,
+                                  None) == sto.STO_EINVAL
     assert lib.sto_run(None, buf, 1, None) == sto.STO_EINVAL
     assert lib.sto_get_info(None, None) == sto.STO_EINVAL
     lib.sto_destroy(None)
