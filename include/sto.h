@@ -322,19 +322,30 @@ typedef struct {
   int32_t candidates;          /* candidates the autotuner timed */
   float tuned_us_per_stage;    /* the winner's time per stage in the tuning run */
   int32_t staged;              /* 1: the epilogue copies the next pair's state to shared memory ahead */
-  int32_t reserved[3];
+  int32_t groups;              /* reservoir groups with their own grid barriers (1 or 2): with 2, one
+                                  group's tensor-core product overlaps the other's update */
+  int32_t reserved[2];
 } sto_batch_plan;
 
-/* Set the plan: tile_n (multiple of 16 in [16, 128]) and slots (3, 6 or 9:
+/* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (3, 6 or 9:
  * three copy warps own every third slot; the state staging buffer is used
- * when it fits beside the ring), or (0, 0) to time every candidate (tile_n
- * in {16, 32, ..., 128} up to R, slots in {3, 6}, staging on and off) on two
- * RK4 steps of zero input from the batch's state
- * (restored afterwards) and keep the fastest.  Tuned plans are cached per
- * (device, N, R) for the life of the process.  The stage state is kept.
+ * when it fits beside the ring), with one reservoir group, or (0, 0) to time
+ * every candidate (tile_n in {16, 32, 40, 48, 64, ..., 128} up to R, slots
+ * in {3, 6}, staging on and off, 1 and 2 groups) on two RK4 steps of zero
+ * input from the batch's state (restored afterwards) and keep the fastest.
+ * Tuned plans are cached per (device, N, R) for the life of the process.
+ * The stage state is kept.
  * Errors: STO_EINVAL, STO_ENOTSUP (plan cannot run: shared memory, tile
  * shape), STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA.  No counterpart in the paper. */
 STO_API int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots);
+
+/* sto_batch_set_plan with the number of reservoir groups (1 or 2; 2 needs at
+ * least two tile columns, i.e. R > tile_n): the tile columns are split into
+ * that many groups, each with its own grid barrier, so that with 2 the
+ * tensor-core product of one group runs while the other group's update
+ * finishes.  (0, 0, any) runs the autotuner.  Errors: as sto_batch_set_plan;
+ * STO_EINVAL for groups outside 1..2. */
+STO_API int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups);
 
 /* The current plan (all zero before the first run or set_plan). */
 STO_API int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out);

@@ -1163,6 +1163,7 @@ int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const f
 // tile), copy-ring depth, CTAs.
 struct SweepPlan {
   int bn = 0, slots = 0, G = 0, tiles_m = 0, tiles_n = 0, acc_cols = 0, staged = 0;
+  int groups = 1, tn_split = 0;  // reservoir groups with their own barriers (see sweep.cuh)
   size_t smem = 0;
 };
 
@@ -1217,18 +1218,23 @@ void free_batch(sto_batch* b) {
   delete b;
 }
 
-// Plan for tile width bn and ring depth slots, or false when it cannot run:
-// bn a multiple of 16 in [16, 256] (tcgen05 M = 128 shapes), shared memory
-// within the device limit, every CTA resident (one per SM).
-bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, SweepPlan* out) {
-  if (bn < 16 || bn > 128 || bn % 16 != 0 || slots < sto::kSpProducers || slots > sto::kSpMaxSlots ||
-      slots % sto::kSpProducers != 0)
+// Plan for tile width bn, ring depth slots and 1 or 2 reservoir groups, or
+// false when it cannot run: bn a multiple of 8 in [16, 128] (the MMA N = 2 bn
+// of the hi/lo stack is a multiple of 16, a tcgen05 M = 128 shape), shared
+// memory within the device limit, every CTA resident (one per SM), and with
+// two groups at least two tile columns.
+bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, SweepPlan* out) {
+  if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < sto::kSpProducers || slots > sto::kSpMaxSlots ||
+      slots % sto::kSpProducers != 0 || groups < 1 || groups > 2)
     return false;
   SweepPlan p;
   p.bn = bn;
   p.slots = slots;
   p.tiles_m = b->Mpad / sto::kSwM;
   p.tiles_n = (b->R + bn - 1) / bn;
+  if (groups == 2 && p.tiles_n < 2) return false;
+  p.groups = groups;
+  p.tn_split = groups == 2 ? (p.tiles_n + 1) / 2 : p.tiles_n;
   p.acc_cols = 2 * bn <= 32 ? 32 : (2 * bn <= 64 ? 64 : (2 * bn <= 128 ? 128 : 256));  // [hi | lo] columns
   p.staged = staged ? 1 : 0;
   p.smem = static_cast<size_t>(slots) * (sto::kSwSliceA + 2u * bn * sto::kSwK * 2u) +
@@ -1246,8 +1252,8 @@ bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, SweepPlan* ou
     return false;
   }
   // balanced grid: the fewest CTAs that keep the most loaded one at the
-  // minimum number of tiles
-  const long long n_tiles = static_cast<long long>(p.tiles_m) * p.tiles_n;
+  // minimum number of tiles (of the larger group)
+  const long long n_tiles = static_cast<long long>(p.tiles_m) * p.tn_split;
   const long long slots_avail = static_cast<long long>(sms) * 1;  // one CTA per SM (928 threads)
   const long long per = (n_tiles + slots_avail - 1) / slots_avail;
   p.G = static_cast<int>((n_tiles + per - 1) / per);
@@ -1315,10 +1321,12 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
   a.tiles_m = p.tiles_m;
   a.tiles_n = p.tiles_n;
   a.acc_cols = p.acc_cols;
+  a.groups = p.groups;
+  a.tn_split = p.tn_split;
   a.staged = p.staged;
   a.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
   set_constants(P, &a.c);
-  STO_CUDA(cudaMemsetAsync(b->gbar, 0, 8, s));
+  STO_CUDA(cudaMemsetAsync(b->gbar, 0, 16, s));  // one counter per group
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.G);
   cfg.blockDim = dim3(sto::kSpThreads);
@@ -1333,9 +1341,10 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
   return STO_OK;
 }
 
-// Tile widths and ring depths the autotuner times.
-constexpr int kTuneBn[] = {16, 32, 48, 64, 80, 96, 112, 128};
+// Tile widths, ring depths and group counts the autotuner times.
+constexpr int kTuneBn[] = {16, 32, 40, 48, 64, 80, 96, 112, 128};
 constexpr int kTuneSlots[] = {3, 6};
+constexpr int kTuneGroups[] = {1, 2};
 
 struct TuneKey {
   int dev;
@@ -1346,9 +1355,10 @@ struct TuneKey {
   }
 };
 
-// Process-wide cache of tuned plans (bn, slots, measured us per stage).
-std::map<TuneKey, std::array<float, 3>>& tune_cache() {
-  static std::map<TuneKey, std::array<float, 3>> m;
+// Process-wide cache of tuned plans (bn, slots * 2 + staged, groups,
+// measured us per stage).
+std::map<TuneKey, std::array<float, 4>>& tune_cache() {
+  static std::map<TuneKey, std::array<float, 4>> m;
   return m;
 }
 std::mutex& tune_mutex() {
@@ -1369,11 +1379,11 @@ int sweep_autotune(sto_batch* b) {
     if (it != tune_cache().end()) {
       SweepPlan p;
       const int code = static_cast<int>(it->second[1]);
-      if (sweep_plan(b, static_cast<int>(it->second[0]), code / 2, code % 2, &p)) {
+      if (sweep_plan(b, static_cast<int>(it->second[0]), code / 2, code % 2, static_cast<int>(it->second[2]), &p)) {
         const int rc = sweep_apply_plan(b, p);
         if (rc) return rc;
         b->tuned = 1;
-        b->tuned_us = it->second[2];
+        b->tuned_us = it->second[3];
         return STO_OK;
       }
     }
@@ -1408,10 +1418,11 @@ int sweep_autotune(sto_batch* b) {
   int rc = STO_OK;
   for (int bn : kTuneBn) {
     if (bn > ((b->R + 15) / 16) * 16) break;  // tiles wider than R only add padding
-    for (int cand = 0; cand < 2 * static_cast<int>(sizeof(kTuneSlots) / sizeof(kTuneSlots[0])); ++cand) {
-      const int slots = kTuneSlots[cand / 2], staged = cand % 2;
+    constexpr int kSlotsN = static_cast<int>(sizeof(kTuneSlots) / sizeof(kTuneSlots[0]));
+    for (int cand = 0; cand < 4 * kSlotsN; ++cand) {
+      const int slots = kTuneSlots[(cand / 2) % kSlotsN], staged = cand % 2, groups = kTuneGroups[cand / (2 * kSlotsN)];
       SweepPlan p;
-      if (!sweep_plan(b, bn, slots, staged, &p)) continue;
+      if (!sweep_plan(b, bn, slots, staged, groups, &p)) continue;
       if ((rc = sweep_apply_plan(b, p)) != STO_OK) break;
       float ms = 0.f;
       for (int rep = 0; rep < 3 && rc == STO_OK; ++rep) {
@@ -1463,7 +1474,8 @@ int sweep_autotune(sto_batch* b) {
   b->candidates = n;
   b->tuned_us = best;
   std::lock_guard<std::mutex> lk(tune_mutex());
-  tune_cache()[key] = {static_cast<float>(best_p.bn), static_cast<float>(best_p.slots * 2 + best_p.staged), best};
+  tune_cache()[key] = {static_cast<float>(best_p.bn), static_cast<float>(best_p.slots * 2 + best_p.staged),
+                       static_cast<float>(best_p.groups), best};
   return STO_OK;
 }
 
@@ -1593,12 +1605,18 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
 }
 
 int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots) {
+  return sto_batch_set_plan_ex(b, tile_n, slots, 1);
+}
+
+int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups) {
   if (!b) return STO_EINVAL;
+  if (groups < 1 || groups > 2) return STO_EINVAL;
   cudaStreamSynchronize(b->stream);
   if (tile_n == 0 && slots == 0) return sweep_autotune(b);
   SweepPlan p;
   // stage the epilogue's state through shared memory when it fits beside the ring
-  if (!sweep_plan(b, tile_n, slots, 1, &p) && !sweep_plan(b, tile_n, slots, 0, &p)) return STO_ENOTSUP;
+  if (!sweep_plan(b, tile_n, slots, 1, groups, &p) && !sweep_plan(b, tile_n, slots, 0, groups, &p))
+    return STO_ENOTSUP;
   int rc = sweep_apply_plan(b, p);
   if (rc) return rc;
   b->tuned = 0;
@@ -1620,6 +1638,7 @@ int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out) {
   out->candidates = b->candidates;
   out->tuned_us_per_stage = b->tuned_us;
   out->staged = b->plan.staged;
+  out->groups = b->plan.groups;
   return STO_OK;
 }
 

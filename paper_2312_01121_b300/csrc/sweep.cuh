@@ -12,15 +12,23 @@
 // shared-memory bandwidth at these widths) and summed in the epilogue.
 //
 // One persistent cooperative launch runs a whole sto_run_batched call.  The
-// product is cut into tiles of 128 oscillators x BN reservoirs; CTA c takes
-// tiles c, c + G, ... of every stage.  Warp 0 streams the K slices of a tile
-// (one W slice and the matching X_hi and X_lo slices, 1-D bulk copies) through
-// a shared-memory ring and issues the MMAs into one of two tensor-memory
-// accumulators; the other 28 warps read the finished accumulator with
-// tcgen05.ld and run the per-pair epilogue (double-float torque, RK4
-// combination, BF16 split of the next X, sampling) while the next tile's MMAs
-// fill the other accumulator.  A stage ends with a grid barrier (every CTA's
-// X for the next stage written) before the next stage's first copy.
+// product is cut into tiles of 128 oscillators x BN reservoirs.  Warp 0
+// issues the MMAs of a tile into one of two tensor-memory accumulators while
+// warps 1-3 stream its K slices (one W slice and the matching X_hi and X_lo
+// slices, 1-D bulk copies) through a shared-memory ring; the other 28 warps
+// read a finished accumulator with tcgen05.ld and run the per-pair epilogue
+// (double-float torque, RK4 combination, BF16 split of the next X, sampling)
+// while the next tile's MMAs fill the other accumulator.
+//
+// Reservoir groups.  Reservoirs are independent: the next stage of a
+// reservoir needs only its own column of D.  The tile columns are split into
+// `groups` (1 or 2) sets, each with its own grid barrier, and the work runs
+// as units (stage g, group q) in the order (0,0), (0,1), (1,0), (1,1), ...
+// Unit (g, q) waits only for every CTA's epilogue of (g-1, q), so with two
+// groups the MMAs of one group run while the epilogue warps finish the
+// other: the tensor-core product and the double-float update overlap
+// instead of following each other across a grid-wide barrier.  CTA c takes
+// tiles c, c + G, ... of each group.
 //
 // Layouts.  Both product operands are kept in global memory in the order
 // the tensor cores read them from shared memory, so one K slice of one tile
@@ -70,9 +78,10 @@ struct SweepArgs {
   const df* hs0_r;           // per reservoir H_s0
   const df* ain_g_r;         // per reservoir g A_in
   int* err;                  // int32[4], as the stepper's
-  unsigned long long* gbar;  // grid barrier counter, zero at launch
+  unsigned long long* gbar;  // one grid barrier counter per group, zero at launch
   int N, R, Kpad, n_in, comp, S, T;
   int bn, slots, tiles_m, tiles_n, acc_cols;  // plan: tile width, ring depth, tiles, TMEM columns per accumulator
+  int groups, tn_split;      // reservoir groups (1 or 2); group 0 = tile columns [0, tn_split)
   int staged;                // 1: the next pair's state is copied to shared memory ahead (cp.async)
   unsigned long long timeout_ns;
   KArgs c;                   // shared constants (gdt, alpha, happl, hkp, lambda, p, acp, sixth)
@@ -208,34 +217,64 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Unit release from the MMA thread to the copy warps: a monotonic counter in
+// shared memory (units released so far).  A counter, not an mbarrier phase:
+// with empty units the MMA thread can release two units before a copy warp
+// looks, which a phase parity cannot tell apart.
+__device__ __forceinline__ void st_release_cta_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.cta.shared::cta.u64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_cta_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.cta.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
 }
 
-// The whole sweep call: 4 S T stages, tiles of this CTA in each.  Warp 0
-// (one thread) waits for the grid barrier, releases the stage to the copy
-// warps and issues the MMAs; warps 1-3 (one thread each) fill their ring
-// slots; warps 4-31 run the epilogue.
+// Tiles of group q: count, and the (tm, tn) of the group's tile `idx`.
+__device__ __forceinline__ int sweep_group_tiles(const SweepArgs& a, int q) {
+  return a.tiles_m * (q == 0 ? a.tn_split : a.tiles_n - a.tn_split);
+}
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int q, int idx, int* tm, int* tn) {
+  *tm = idx % a.tiles_m;
+  *tn = idx / a.tiles_m + (q == 0 ? 0 : a.tn_split);
+}
+
+// The whole sweep call: 4 S T stages of every group.  Warp 0 (one thread)
+// passes each unit's group barrier, releases the unit to the copy warps and
+// issues the MMAs; warps 1-3 (one thread each) fill their ring slots; warps
+// 4-31 run the epilogue.
 __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
   // the swizzle pattern repeats every 1024 B: the ring starts on such a boundary
   unsigned char* sp_smem = sp_smem_raw + ((1024u - (smem_u32(sp_smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t full[kSpMaxSlots], empty[kSpMaxSlots], acc_full[2], acc_empty[2];
-  __shared__ uint64_t stage_done, stage_go, drain;
+  __shared__ uint64_t stage_done[2], drain;
+  __shared__ unsigned long long s_go;  // units released to the copy warps
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, cta = blockIdx.x;
-  const int n_tiles = a.tiles_m * a.tiles_n;
-  const int n_my = cta < n_tiles ? (n_tiles - 1 - cta) / G + 1 : 0;
+  const int n_grp = a.groups;
+  // this CTA's tiles of each group, and the CTAs with tiles in each group
+  const int T0 = sweep_group_tiles(a, 0), T1 = n_grp > 1 ? sweep_group_tiles(a, 1) : 0;
+  const int my0 = cta < T0 ? (T0 - 1 - cta) / G + 1 : 0, my1 = cta < T1 ? (T1 - 1 - cta) / G + 1 : 0;
+  const int G0 = T0 < G ? T0 : G, G1 = T1 < G ? T1 : G;
+  auto n_my = [&](int q) { return q == 0 ? my0 : my1; };
   const int nk = a.Kpad / kSwK;
-  const int L = n_my * nk;  // K slices of this CTA per stage
+  const long long L0 = static_cast<long long>(my0) * nk, L1 = static_cast<long long>(my1) * nk;
   const uint32_t sliceB = static_cast<uint32_t>(a.bn) * kSwK * 2;  // one X slice (hi or lo)
   const uint32_t slot_bytes = kSwSliceA + 2 * sliceB;
   const long long n_stages = 4LL * a.S * a.T;
+  const long long n_units = n_stages * n_grp;
   const volatile int* abort_flag = &s_abort;
+  // ring position of the first K slice of unit u = (g, q)
+  auto unit_base = [&](long long g, int q) -> long long { return g * (L0 + L1) + (q == 1 ? L0 : 0); };
 
   if (tid == 0) {
     for (int s = 0; s < a.slots; ++s) {
@@ -245,10 +284,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], kSpEpiWarps);
+      mbar_init(&stage_done[b], kSpEpiWarps);
     }
-    mbar_init(&stage_done, kSpEpiWarps);
-    mbar_init(&stage_go, 1);
     mbar_init(&drain, 1);
+    s_go = 0;
     s_abort = 0;
     fence_mbar_init();
   }
@@ -266,23 +305,26 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------------------------------------- grid barrier and MMAs
+      // ----------------------------------------- group barriers and MMAs
       const uint32_t idesc = umma_idesc_bf16(kSwM, 2 * a.bn);  // [X_hi | X_lo] rows
-      long long tiles_done = 0;  // accumulator sequence number of the stage's first tile
+      long long seq = 0;  // accumulator sequence number of the unit's first tile
       bool ok = true;
-      for (long long g = 0; g < n_stages && ok; ++g) {
-        if (g > 0) {
-          // grid barrier: this CTA's epilogue of stage g-1 is done (its X
-          // for stage g written), then every CTA's
-          if (n_my > 0 &&
-              !mbar_wait_bounded(&stage_done, static_cast<uint32_t>((g - 1) & 1), a.timeout_ns, abort_flag)) {
+      for (long long u = 0; u < n_units && ok; ++u) {
+        const long long g = u / n_grp;
+        const int q = static_cast<int>(u % n_grp);
+        const int nm = n_my(q);
+        if (g > 0 && nm > 0) {
+          // group barrier: this CTA's epilogue of (g-1, q) is done (its X of
+          // the group for stage g written), then every CTA's of the group
+          if (!mbar_wait_bounded(&stage_done[q], static_cast<uint32_t>((g - 1) & 1), a.timeout_ns, abort_flag)) {
             ok = false;
             break;
           }
-          red_release_add(a.gbar, 1ull);
-          const unsigned long long target = static_cast<unsigned long long>(G) * static_cast<unsigned long long>(g);
+          red_release_add(a.gbar + q, 1ull);
+          const unsigned long long target =
+              static_cast<unsigned long long>(q == 0 ? G0 : G1) * static_cast<unsigned long long>(g);
           const unsigned long long t0 = gtimer();
-          for (uint32_t n = 1; ld_acquire_u64(a.gbar) < target; ++n) {
+          for (uint32_t n = 1; ld_acquire_u64(a.gbar + q) < target; ++n) {
             if ((n & 31u) == 0) {
               if (ld_relaxed_i32(a.err) != 0 || gtimer() - t0 > a.timeout_ns) {
                 ok = false;
@@ -293,15 +335,16 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           if (!ok) break;
           fence_proxy_async_global();
         }
-        mbar_arrive(&stage_go);  // the copy warps may read this stage's X
-        const long long base = g * L;
+        st_release_cta_u64(&s_go, static_cast<unsigned long long>(u + 1));  // the copy warps may read this unit's X
+        const long long base = unit_base(g, q);
+        const int L = nm * nk;
         for (int lq = 0; lq < L; ++lq) {
           const int i = lq / nk, j = lq % nk;
-          const long long seq = tiles_done + i;
-          const int b = static_cast<int>(seq & 1);
-          if (j == 0 && seq >= 2) {
+          const long long sq = seq + i;
+          const int b = static_cast<int>(sq & 1);
+          if (j == 0 && sq >= 2) {
             // the epilogue has read this accumulator's previous tile
-            if (!mbar_wait_bounded(&acc_empty[b], static_cast<uint32_t>(((seq >> 1) - 1) & 1), a.timeout_ns,
+            if (!mbar_wait_bounded(&acc_empty[b], static_cast<uint32_t>(((sq >> 1) - 1) & 1), a.timeout_ns,
                                    abort_flag)) {
               ok = false;
               break;
@@ -332,7 +375,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           umma_commit(&empty[s]);
           if (j == nk - 1) umma_commit(&acc_full[b]);
         }
-        tiles_done += n_my;
+        seq += nm;
       }
       if (!ok) {
         if (!*abort_flag) report_error(a.err, kErrTimeout, cta, 0u, kSiteFull);
@@ -351,13 +394,23 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
       const uint64_t pol = policy_evict_last();
       long long last = -1;  // last position issued
       bool ok = true;
-      for (long long g = 0; g < n_stages && ok; ++g) {
-        if (!mbar_wait_bounded(&stage_go, static_cast<uint32_t>(g & 1), a.timeout_ns, abort_flag)) {
-          ok = false;
-          break;
+      for (long long u = 0; u < n_units && ok; ++u) {
+        if (ld_acquire_cta_u64(&s_go) <= static_cast<unsigned long long>(u)) {
+          const unsigned long long t0 = gtimer();
+          for (uint32_t n = 1; ld_acquire_cta_u64(&s_go) <= static_cast<unsigned long long>(u); ++n) {
+            if ((n & 15u) == 0 && (*abort_flag || gtimer() - t0 > a.timeout_ns)) {
+              ok = false;
+              break;
+            }
+          }
+          if (!ok) break;
         }
+        fence_proxy_async_global();  // the released X writes, before this warp's bulk copies read them
+        const long long g = u / n_grp;
+        const int q = static_cast<int>(u % n_grp);
         const __nv_bfloat16* X = (g & 1) ? a.X1 : a.X0;
-        const long long base = g * L;
+        const long long base = unit_base(g, q);
+        const int L = n_my(q) * nk;
         const int lp0 = static_cast<int>(((pid - base % kSpProducers) % kSpProducers + kSpProducers) % kSpProducers);
         for (int lp = lp0; lp < L; lp += kSpProducers) {
           const long long P = base + lp;
@@ -369,8 +422,8 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
             break;
           }
           const int i = lp / nk, j = lp % nk;
-          const int tile = cta + i * G;
-          const int tm = tile % a.tiles_m, tn = tile / a.tiles_m;
+          int tm, tn;
+          sweep_tile(a, q, cta + i * G, &tm, &tn);
           unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
           const __nv_bfloat16* xt = X + static_cast<size_t>(tn) * 2 * nk * (a.bn * kSwK);
           mbar_arrive_expect_tx(&full[s], slot_bytes);
@@ -403,16 +456,19 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
                                             static_cast<size_t>(warp - kSpEpiFirst) * kSpStageBytes);
     long long seq = 0;
     bool ok = true;
-    // a CTA without tiles has no epilogue (the host never plans one)
-    for (long long g = 0; g < n_stages && ok && n_my > 0; ++g) {
+    for (long long u = 0; u < n_units && ok; ++u) {
+      const long long g = u / n_grp;
+      const int q = static_cast<int>(u % n_grp);
+      const int nm = n_my(q);
+      if (nm == 0) continue;  // no tiles of this group here (and no barrier arrival)
       const int st = static_cast<int>(g & 3);
       const long long step = g >> 2;
       const int t = static_cast<int>(step / a.S);
       const bool sample = (step % a.S) == a.S - 1;
       __nv_bfloat16* Xn = (g & 1) ? a.X0 : a.X1;  // the next stage's operand
-      for (int i = 0; i < n_my; ++i, ++seq) {
-        const int tile = cta + i * G;
-        const int tm = tile % a.tiles_m, tn = tile / a.tiles_m;
+      for (int i = 0; i < nm; ++i, ++seq) {
+        int tm, tn;
+        sweep_tile(a, q, cta + i * G, &tm, &tn);
         const int b = static_cast<int>(seq & 1);
         const unsigned k = static_cast<unsigned>(tm * kSwM + 32 * q4 + lane);
         const bool row_ok = k < static_cast<unsigned>(a.N);
@@ -436,11 +492,11 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           if (row_ok && r < static_cast<unsigned>(a.R)) {
             const size_t idx = static_cast<size_t>(r) * a.N + k;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              cp_async8(stg + (q * 32 + lane), a.mn + q * RN + idx);
+            for (int qq = 0; qq < 3; ++qq) {
+              cp_async8(stg + (qq * 32 + lane), a.mn + qq * RN + idx);
               if (st > 0) {
-                cp_async8(stg + ((3 + q) * 32 + lane), a.ms + q * RN + idx);
-                cp_async8(stg + ((6 + q) * 32 + lane), a.ksum + q * RN + idx);
+                cp_async8(stg + ((3 + qq) * 32 + lane), a.ms + qq * RN + idx);
+                cp_async8(stg + ((6 + qq) * 32 + lane), a.ksum + qq * RN + idx);
               }
             }
           }
@@ -471,26 +527,26 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           if (a.staged) {
             cp_async_wait_all();
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              const float2 x0 = stg[q * 32 + lane];
-              mn[q] = df{x0.x, x0.y};
+            for (int qq = 0; qq < 3; ++qq) {
+              const float2 x0 = stg[qq * 32 + lane];
+              mn[qq] = df{x0.x, x0.y};
               if (st > 0) {
-                const float2 x1 = stg[(3 + q) * 32 + lane], x2 = stg[(6 + q) * 32 + lane];
-                ms[q] = df{x1.x, x1.y};
-                ks[q] = df{x2.x, x2.y};
+                const float2 x1 = stg[(3 + qq) * 32 + lane], x2 = stg[(6 + qq) * 32 + lane];
+                ms[qq] = df{x1.x, x1.y};
+                ks[qq] = df{x2.x, x2.y};
               }
             }
             if (jc + kSpEpiPerQuarter < a.bn) prefetch(jc + kSpEpiPerQuarter);
           } else if (pair_ok) {
             const size_t idx = static_cast<size_t>(r) * a.N + k;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              const float2 x0 = a.mn[q * RN + idx];
-              mn[q] = df{x0.x, x0.y};
+            for (int qq = 0; qq < 3; ++qq) {
+              const float2 x0 = a.mn[qq * RN + idx];
+              mn[qq] = df{x0.x, x0.y};
               if (st > 0) {
-                const float2 x1 = a.ms[q * RN + idx], x2 = a.ksum[q * RN + idx];
-                ms[q] = df{x1.x, x1.y};
-                ks[q] = df{x2.x, x2.y};
+                const float2 x1 = a.ms[qq * RN + idx], x2 = a.ksum[qq * RN + idx];
+                ms[qq] = df{x1.x, x1.y};
+                ks[qq] = df{x2.x, x2.y};
               }
             }
           }
@@ -504,9 +560,9 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         if (lane == 0) mbar_arrive(&acc_empty[b]);
       }
       if (!ok) break;
-      fence_proxy_async_global();  // this stage's X writes, before the copies of the next
+      fence_proxy_async_global();  // this unit's X writes, before the copies of the next
       __syncwarp();
-      if (lane == 0) mbar_arrive(&stage_done);
+      if (lane == 0) mbar_arrive(&stage_done[q]);
     }
     if (!ok && lane == 0) {
       if (!*abort_flag) report_error(a.err, kErrTimeout, cta, 0u, kSiteFull);

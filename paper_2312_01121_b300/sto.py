@@ -54,7 +54,7 @@ class sto_batch_plan(ctypes.Structure):
     _fields_ = [("tile_n", ctypes.c_int32), ("slots", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("tiles", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("tuned", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("tuned_us_per_stage", ctypes.c_float),
-                ("staged", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("staged", ctypes.c_int32), ("groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
@@ -107,6 +107,7 @@ SIGNATURES = {
     "sto_batch_get_state": (ctypes.c_int, [_VP, _VP]),
     "sto_batch_destroy": (None, [_VP]),
     "sto_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32]),
+    "sto_batch_set_plan_ex": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
     "sto_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(sto_batch_plan)]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
@@ -484,9 +485,10 @@ class Sweep:
         _check(load_library().sto_batch_get_state(self.handle, out.ctypes.data))
         return out
 
-    def set_plan(self, tile_n: int = 0, slots: int = 0):
-        """Force a tile width / ring depth, or (0, 0) to run the autotuner."""
-        _check(load_library().sto_batch_set_plan(self.handle, int(tile_n), int(slots)))
+    def set_plan(self, tile_n: int = 0, slots: int = 0, groups: int = 1):
+        """Force a tile width / ring depth / reservoir-group count, or (0, 0)
+        to run the autotuner."""
+        _check(load_library().sto_batch_set_plan_ex(self.handle, int(tile_n), int(slots), int(groups)))
 
     def plan(self) -> dict:
         p = sto_batch_plan()

@@ -117,9 +117,12 @@ def test_group_of_own_w_reservoirs_matches_separate_runs(sto):
     assert np.max(np.abs(outs[0] - orc)) <= 1e-5
 
 
-@pytest.mark.parametrize("tile_n,slots", [(16, 3), (32, 6), (48, 3), (80, 3), (80, 6), (112, 3), (128, 3)])
-def test_sweep_forced_plans_match_oracle(sto, tile_n, slots):
-    """Every tile width and ring depth gives the oracle's states (ragged N and R)."""
+@pytest.mark.parametrize("tile_n,slots,groups", [(16, 3, 1), (32, 6, 1), (48, 3, 1), (80, 3, 1), (80, 6, 1),
+                                                 (112, 3, 1), (128, 3, 1), (16, 6, 2), (24, 3, 2), (40, 3, 2),
+                                                 (48, 3, 2)])
+def test_sweep_forced_plans_match_oracle(sto, tile_n, slots, groups):
+    """Every tile width, ring depth and group count gives the oracle's states
+    (ragged N and R; with 2 groups of unequal size for 16, 24 and 48)."""
     N, R, T = 300, 70, 2
     W, w_in, _, u = make_system(N, "gauss", seed=11, T=T)
     rng = np.random.default_rng(11)
@@ -128,9 +131,9 @@ def test_sweep_forced_plans_match_oracle(sto, tile_n, slots):
     P = sto.Params(substeps=3, A_cp=100.0, A_in=30.0)
     st = np.zeros((T, R, N), np.float32)
     with sto.Sweep(W, w_in, P, currents=cur, gains=gain) as sw:
-        sw.set_plan(tile_n, slots)
+        sw.set_plan(tile_n, slots, groups)
         plan = sw.plan()
-        assert (plan["tile_n"], plan["slots"], plan["tuned"]) == (tile_n, slots, 0)
+        assert (plan["tile_n"], plan["slots"], plan["tuned"], plan["groups"]) == (tile_n, slots, 0, groups)
         assert plan["staged"] in (0, 1)
         assert plan["tiles"] == -(-N // 128) * -(-R // tile_n)
         sw.run(u, st)
@@ -168,20 +171,52 @@ def test_sweep_autotuner_and_invalid_plans(sto):
     N, R, T = 500, 130, 1
     W, w_in, _, u = make_system(N, "gauss", seed=13, T=T)
     P = sto.Params(substeps=2)
+    with sto.Sweep(W, w_in, P, currents=np.full(64, 2e-3)) as sw:
+        with pytest.raises(sto.StoError):
+            sw.set_plan(64, 3, 2)  # R = 64 is one tile column: nothing to split into groups
     with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw:
         assert sw.plan()["tile_n"] == 0  # no plan before the first run
         with pytest.raises(sto.StoError):
-            sw.set_plan(40, 3)  # not a multiple of 16
+            sw.set_plan(36, 3)  # not a multiple of 8
+        with pytest.raises(sto.StoError):
+            sw.set_plan(64, 3, 3)  # at most two reservoir groups
         with pytest.raises(sto.StoError):
             sw.set_plan(64, 9)  # ring deeper than the kernel allows
         st = np.zeros((T, R, N), np.float32)
         sw.run(u, st)
         plan = sw.plan()
         assert plan["tuned"] == 1 and plan["candidates"] >= 1 and plan["tuned_us_per_stage"] > 0
-        assert plan["tile_n"] % 16 == 0 and plan["grid"] <= torch.cuda.get_device_properties(0).multi_processor_count
+        assert plan["tile_n"] % 8 == 0 and plan["grid"] <= torch.cuda.get_device_properties(0).multi_processor_count
+        assert plan["groups"] in (1, 2)
         # the tuner restored the state it ran from: same samples as a forced plan
         ref = np.zeros_like(st)
         with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw2:
-            sw2.set_plan(plan["tile_n"], plan["slots"])
+            sw2.set_plan(plan["tile_n"], plan["slots"], plan["groups"])
             sw2.run(u, ref)
         assert np.array_equal(st, ref)
+
+
+@pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3),
+                                              (1000, 65, 32, 6)])
+def test_sweep_two_groups_bitwise_equal_to_one(sto, N, R, tile_n, slots):
+    """Two reservoir groups with their own barriers only reorder independent
+    work: every tile's product and every pair's update are the same
+    arithmetic, so the samples and the final state are the same bits as with
+    one grid-wide barrier (including several tiles per CTA per group, and a
+    second group with fewer tiles than the first)."""
+    T = 2
+    W, w_in, _, u = make_system(N, "gauss", seed=N + R, T=T)
+    rng = np.random.default_rng(N + R)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=3, A_cp=60.0, A_in=20.0)
+    out = []
+    for groups in (1, 2):
+        st = np.zeros((T, R, N), np.float32)
+        with sto.Sweep(W, w_in, P, currents=cur, gains=gain) as sw:
+            sw.set_plan(tile_n, slots, groups)
+            assert sw.plan()["groups"] == groups
+            sw.run(u, st)
+            out.append((st, sw.state()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
