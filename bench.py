@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
+    ap.add_argument("--group-lanes", type=int, default=0, help="lanes of the group launch (0 = auto)")
     ap.add_argument("--adj-n", type=int, default=1000)
     ap.add_argument("--adj-t", type=int, default=40, help="input samples per adjoint call")
     ap.add_argument("--adj-k", type=int, default=20, help="checkpoint interval (samples)")
@@ -372,8 +373,10 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
 
 
 def time_group(args, seed, torch, sto, dev, hbm_peak):
-    """sto_run_group: R reservoirs with their own Gaussian W and N ~ U[100, 4000]
-    (the own-W half of the sweep), one graph-captured call per T samples."""
+    """R reservoirs with their own Gaussian W and N ~ U[100, 4000] (the own-W
+    half of the sweep), one persistent launch per call of T samples
+    (sto_group_run, lanes of CTAs running members side by side); the same
+    members as a graph of one launch per member (sto_run_group) beside it."""
     rng = np.random.default_rng([seed, 11])
     Ns = rng.integers(100, 4001, args.group_r)
     T = args.group_t
@@ -386,16 +389,24 @@ def time_group(args, seed, torch, sto, dev, hbm_peak):
         res.append(sto.Reservoir(torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), P,
                                  m0=torch.from_numpy(m0).to(dev), stream=stream))
     u_d = torch.from_numpy(u).to(dev)
-    sto.sto_run_group(res, u_d[:T], T)  # warm-up
-    torch.cuda.synchronize()
     reps = 2
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(reps):
-        sto.sto_run_group(res, u_d[T * (i + 1):T * (i + 2)], T)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+
+    def timed(call):
+        call(u_d[:T])  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(reps):
+            call(u_d[T * (i + 1):T * (i + 2)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_graph = timed(lambda uu: sto.sto_run_group(res, uu, T))
+    grp = sto.Group(res, lanes=args.group_lanes)
+    info = grp.info()
+    ms = timed(lambda uu: grp.run(uu, T))
+    grp.close()
     for r in res:
         r.close()
     stages = 4 * args.substeps * T
@@ -407,7 +418,9 @@ def time_group(args, seed, torch, sto, dev, hbm_peak):
             "ms_per_call": ms, "us_per_stage": ms * 1e3 / stages,
             "w_gbs_algorithmic": wbytes * stages / (ms / 1e3) / 1e9,
             "frac_of_hbm": wbytes * stages / (ms / 1e3) / 1e9 / hbm_peak,
-            "note": "W of every reservoir is at most 64 MB and is kept in L2 between stages"}
+            "launches_per_call": 1, "lanes": info["lanes"], "lane_width": info["lane_width"],
+            "graph_of_launches_us_per_stage": ms_graph * 1e3 / stages,
+            "note": "one cooperative launch; members on different lanes run side by side"}
 
 
 def time_fp64(args, seed, torch, sto, dev, hbm_peak):

@@ -259,6 +259,48 @@ STO_API int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* d
 STO_API int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
                           float* const* states_out);
 
+/* ------------------------------------------------------------------------
+ * A group of reservoirs with their own W (the uneven-N, own-W half of a
+ * parameter sweep; Sec. 1 and Sec. 2: exploring the parameter space is the
+ * time-consuming part) advanced by ONE persistent cooperative launch per
+ * call.  The grid is cut into `lanes` lanes of SMs/lanes CTAs; each lane runs
+ * its reservoirs one after another, each on all of the lane's CTAs, so
+ * reservoirs on different lanes run at the same time (small reservoirs,
+ * which are latency-bound alone, share the GPU instead of holding all of
+ * it).  Reservoirs are assigned to lanes longest first onto the least
+ * loaded lane.  Results equal sto_run's on a handle with the same launch
+ * plan (grid = the lane width) bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct sto_group sto_group; /* opaque */
+
+/* Make a group of n distinct handles (same device, same n_in, FP32
+ * coupling).  lanes = 0 picks the largest lane count up to min(n, 8) for
+ * which every reservoir has at least one oscillator per CTA and at most 120
+ * per CTA.  Each handle is re-planned for the lane width (its W re-tiled on
+ * the device; sto_run on it keeps working, with that plan, and gives the
+ * group's bits; a different plan can change the coupling sums' last bits).  The
+ * group keeps the handle pointers: destroy the group before its handles.
+ * Errors: STO_EINVAL (null, duplicate handles, mismatched n_in or device),
+ *         STO_ENOTSUP (an FP64 handle, or no lane count fits), STO_ENOMEM,
+ *         STO_ECUDA. */
+STO_API int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group** out);
+
+/* Advance every member over the same T input samples u (T x n_in, host or
+ * device); states_out[i] (T x N_i, host or device, or NULL; states_out
+ * itself may be NULL) receives member i's samples.  One cooperative launch;
+ * the call synchronises the first member's stream once at the start (to
+ * reuse its argument records) and once at the end.
+ * Errors: STO_EINVAL, STO_ENOTSUP (a member re-planned or given a tableau
+ *         since creation), STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA. */
+STO_API int sto_group_run(sto_group* g, const float* u, int64_t T, float* const* states_out);
+
+/* The lane count, the CTAs per lane, and (lane_of, n entries, or NULL) the
+ * lane each member runs on.  Errors: STO_EINVAL. */
+STO_API int sto_group_get_info(const sto_group* g, int32_t* lanes, int32_t* lane_width, int32_t* lane_of);
+
+/* Release the group (not its handles; NULL is allowed). */
+STO_API void sto_group_destroy(sto_group* g);
+
 /* Use an explicit Runge-Kutta method other than classic RK4 (Sec. 3.2 uses
  * classic RK4; the paper's conclusion notes that the approach applies to
  * any reservoir evolved by an explicit method).  stages = s in 1..4;

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <array>
 #include <map>
 #include <mutex>
@@ -708,6 +709,75 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
   return STO_OK;
 }
 
+// Re-plan a handle for G CTAs (a lane of a group launch): new plan, W
+// re-tiled on the device.  A lane of a warp sums the same columns of a row
+// in the same order under any plan, except that a plan holding W on chip
+// with at most two rows per warp keeps four partial sums per row: the new
+// plan can change the last bits of the coupling sums.
+int replan_handle(sto_handle* h, int G) {
+  if (h->plan.G == G) return STO_OK;
+  int smem_optin = 0;
+  STO_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  Plan p;
+  int rc = make_plan(h->N, G, h->sm_count, static_cast<size_t>(smem_optin), &p, h->wmode);
+  if (rc) return rc;
+  if (p.P != h->plan.P) return STO_ENOTSUP;
+  const size_t elems = static_cast<size_t>(h->N) * p.P * sto::kPanelCols;
+  float* d_new = nullptr;
+  if (cudaMalloc(&d_new, elems * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return STO_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(d_new, 0, elems * 4, h->stream);
+  if (e == cudaSuccess) {
+    long long blocks = static_cast<long long>((elems + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    sto::retile_w_kernel<<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
+        h->d_W, d_new, static_cast<int>(h->N), p.P, h->plan.G, G);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(d_new);
+    return cuda_fail(e);
+  }
+  cudaFree(h->d_W);
+  h->d_W = d_new;
+  h->plan = p;
+  cudaFree(h->d_WT);  // the adjoint's W^T follows the plan; rebuilt on demand
+  h->d_WT = nullptr;
+  return STO_OK;
+}
+
+}  // namespace
+
+// A fixed set of reservoirs run by one cooperative launch per call (see
+// sto_group_kernel): lanes of CTAs, each running its reservoirs in turn.
+struct sto_group {
+  std::vector<sto_handle*> hs;
+  int n = 0, lanes = 1, width = 1;
+  size_t smem = 0;
+  std::vector<int> lane_begin, order, rpw;
+  sto::KArgs* d_jobs = nullptr;
+  sto::KArgs* h_jobs = nullptr;  // pinned staging of the job records
+  int* d_tab = nullptr;          // lane_begin | order | rpw
+  int* d_errs = nullptr;         // 4 ints per reservoir
+  int* h_errs = nullptr;         // pinned
+  float* d_u = nullptr;
+  size_t d_u_cap = 0;
+};
+
+namespace {
+void free_group(sto_group* g) {
+  if (!g) return;
+  cudaFree(g->d_jobs);
+  cudaFree(g->d_tab);
+  cudaFree(g->d_errs);
+  cudaFree(g->d_u);
+  if (g->h_jobs) cudaFreeHost(g->h_jobs);
+  if (g->h_errs) cudaFreeHost(g->h_errs);
+  delete g;
+}
 }  // namespace
 
 extern "C" {
@@ -1045,6 +1115,203 @@ int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
     if (hs[i]->h_err[0] != 0) return hs[i]->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
   }
   return STO_OK;
+}
+
+int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group** out) {
+  if (!out) return STO_EINVAL;
+  *out = nullptr;
+  if (!hs || n < 1 || lanes < 0) return STO_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || hs[i]->params.n_in != hs[0]->params.n_in || hs[i]->device != hs[0]->device) return STO_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return STO_EINVAL;
+    if (hs[i]->wmode != sto::kWf32) return STO_ENOTSUP;  // the group kernel runs the FP32 coupling
+  }
+  const int sms = hs[0]->sm_count;
+  int64_t n_min = hs[0]->N, n_max = hs[0]->N;
+  for (int i = 0; i < n; ++i) {
+    n_min = hs[i]->N < n_min ? hs[i]->N : n_min;
+    n_max = hs[i]->N > n_max ? hs[i]->N : n_max;
+  }
+  // lanes of `width` CTAs: every reservoir needs at least one oscillator per
+  // CTA and at most 8 rows per consumer warp (120 per CTA)
+  auto fits = [&](int L) {
+    const int w = sms / L;
+    return L >= 1 && w >= 1 && n_min >= w && (n_max + w - 1) / w <= 8 * sto::kConsWarps;
+  };
+  int L = lanes;
+  if (L == 0) {
+    for (L = n < 8 ? n : 8; L > 1 && !fits(L); --L) {
+    }
+  }
+  if (L > sms || !fits(L)) return STO_ENOTSUP;
+  sto_group* g = new (std::nothrow) sto_group();
+  if (!g) return STO_ENOMEM;
+  g->hs.assign(hs, hs + n);
+  g->n = n;
+  g->lanes = L;
+  g->width = sms / L;
+  for (int i = 0; i < n; ++i) {
+    const int rc = replan_handle(hs[i], g->width);
+    if (rc) {
+      free_group(g);
+      return rc;
+    }
+    const int rpw = hs[i]->plan.rpw <= 1 ? 1 : (hs[i]->plan.rpw <= 2 ? 2 : (hs[i]->plan.rpw <= 4 ? 4 : 8));
+    g->rpw.push_back(rpw);
+    g->smem = hs[i]->plan.smem > g->smem ? hs[i]->plan.smem : g->smem;
+  }
+  // longest processing time first onto the least loaded lane; a reservoir's
+  // time is its stage count times the larger of the exchange latency (about
+  // 2.5 us per stage) and streaming its W at ~90 GB/s per CTA
+  std::vector<double> cost(n), load(L, 0.0);
+  std::vector<std::vector<int>> lane_jobs(L);
+  for (int i = 0; i < n; ++i) {
+    const double w_s = 4.0 * static_cast<double>(hs[i]->N) * hs[i]->N / (g->width * 90e9);
+    cost[i] = (w_s > 2.5e-6 ? w_s : 2.5e-6) * hs[i]->rk_stages * hs[i]->params.substeps;
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (int i : idx) {
+    int best = 0;
+    for (int l = 1; l < L; ++l)
+      if (load[l] < load[best]) best = l;
+    load[best] += cost[i];
+    lane_jobs[best].push_back(i);
+  }
+  g->lane_begin.push_back(0);
+  for (int l = 0; l < L; ++l) {
+    for (int j : lane_jobs[l]) g->order.push_back(j);
+    g->lane_begin.push_back(static_cast<int>(g->order.size()));
+  }
+  // device tables
+  const size_t tab_n = g->lane_begin.size() + g->order.size() + g->rpw.size();
+  std::vector<int> tab;
+  tab.insert(tab.end(), g->lane_begin.begin(), g->lane_begin.end());
+  tab.insert(tab.end(), g->order.begin(), g->order.end());
+  tab.insert(tab.end(), g->rpw.begin(), g->rpw.end());
+  cudaStream_t s = hs[0]->stream;
+  cudaError_t e = cudaMalloc(&g->d_jobs, sizeof(sto::KArgs) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_tab, sizeof(int) * tab_n);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_errs, sizeof(int) * 4 * n);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_jobs, sizeof(sto::KArgs) * n);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_errs, sizeof(int) * 4 * n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_tab, tab.data(), sizeof(int) * tab_n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_group(g);
+    return e == cudaErrorMemoryAllocation ? STO_ENOMEM : cuda_fail(e);
+  }
+  *out = g;
+  return STO_OK;
+}
+
+int sto_group_run(sto_group* g, const float* u, int64_t T, float* const* states_out) {
+  if (!g || T < 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  if (!u || T > (1LL << 31) - 1) return u ? STO_ENOTSUP : STO_EINVAL;
+  const int n = g->n;
+  sto_handle* h0 = g->hs[0];
+  cudaStream_t s0 = h0->stream;
+  for (int i = 0; i < n; ++i) {
+    sto_handle* h = g->hs[i];
+    // planned for the lane, classic RK4, FP32 coupling (a tableau set since
+    // creation or a re-planned handle cannot run here)
+    if (!h->rk_classic || h->wmode != sto::kWf32 || h->plan.G != g->width) return STO_ENOTSUP;
+    const uint64_t stages = 4ULL * static_cast<uint64_t>(h->params.substeps) * static_cast<uint64_t>(T);
+    if (stages > 0x40000000ULL) return STO_ENOTSUP;
+    if (h->params.n_in != h0->params.n_in) return STO_EINVAL;
+  }
+  const size_t n_u = static_cast<size_t>(T) * h0->params.n_in;
+  const float* d_u = u;
+  if (!is_device_ptr(u)) {
+    int rc = grow(&g->d_u, &g->d_u_cap, n_u);
+    if (rc) return rc;
+    STO_CUDA(cudaMemcpyAsync(g->d_u, u, n_u * 4, cudaMemcpyHostToDevice, s0));
+    d_u = g->d_u;
+  }
+  std::vector<float*> d_states(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    float* so = states_out ? states_out[i] : nullptr;
+    d_states[i] = so;
+    if (so && !is_device_ptr(so)) {
+      int rc = grow(&g->hs[i]->d_states, &g->hs[i]->d_states_cap, static_cast<size_t>(T) * g->hs[i]->N);
+      if (rc) return rc;
+      d_states[i] = g->hs[i]->d_states;
+    }
+  }
+  STO_CUDA(cudaStreamSynchronize(s0));  // the pinned job records are free to rewrite
+  for (int i = 0; i < n; ++i) {
+    sto::KArgs a = base_args(g->hs[i], d_u, T);  // may reset the exchange buffer on the member's stream
+    a.states_out = d_states[i];
+    a.err = g->d_errs + 4 * i;
+    g->h_jobs[i] = a;
+  }
+  // the launch follows every member's earlier work
+  cudaEvent_t ev = nullptr;
+  STO_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaSuccess;
+  for (int i = 1; i < n && e == cudaSuccess; ++i) {
+    if (g->hs[i]->stream == s0) continue;
+    e = cudaEventRecord(ev, g->hs[i]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev, 0);
+  }
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  STO_CUDA(cudaMemcpyAsync(g->d_jobs, g->h_jobs, sizeof(sto::KArgs) * n, cudaMemcpyHostToDevice, s0));
+  STO_CUDA(cudaMemsetAsync(g->d_errs, 0, sizeof(int) * 4 * n, s0));
+  sto::GroupArgs ga{};
+  ga.jobs = g->d_jobs;
+  ga.lane_begin = g->d_tab;
+  ga.order = g->d_tab + g->lane_begin.size();
+  ga.rpw = g->d_tab + g->lane_begin.size() + g->order.size();
+  ga.n_lanes = g->lanes;
+  ga.lane_width = g->width;
+  const int room = raise_dyn_smem_cap(sto::sto_group_kernel);
+  if (room < static_cast<int>(g->smem)) return STO_ENOTSUP;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g->lanes * g->width);
+  cfg.blockDim = dim3(sto::kThreads);
+  cfg.dynamicSmemBytes = g->smem;
+  cfg.stream = s0;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every lane's CTAs resident together
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  STO_CUDA(cudaLaunchKernelEx(&cfg, sto::sto_group_kernel, ga));
+  STO_CUDA(cudaMemcpyAsync(g->h_errs, g->d_errs, sizeof(int) * 4 * n, cudaMemcpyDeviceToHost, s0));
+  for (int i = 0; i < n; ++i) {
+    float* so = states_out ? states_out[i] : nullptr;
+    if (so && so != d_states[i])
+      STO_CUDA(cudaMemcpyAsync(so, d_states[i], static_cast<size_t>(T) * g->hs[i]->N * 4, cudaMemcpyDeviceToHost,
+                               s0));
+  }
+  STO_CUDA(cudaStreamSynchronize(s0));
+  int rc = STO_OK;
+  for (int i = 0; i < n; ++i) {
+    g->hs[i]->inject_cta = -1;
+    if (g->h_errs[4 * i] != 0 && rc == STO_OK) rc = g->h_errs[4 * i] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  }
+  return rc;
+}
+
+int sto_group_get_info(const sto_group* g, int32_t* lanes, int32_t* lane_width, int32_t* lane_of) {
+  if (!g) return STO_EINVAL;
+  if (lanes) *lanes = g->lanes;
+  if (lane_width) *lane_width = g->width;
+  if (lane_of)
+    for (int l = 0; l < g->lanes; ++l)
+      for (int k = g->lane_begin[l]; k < g->lane_begin[l + 1]; ++k) lane_of[g->order[k]] = l;
+  return STO_OK;
+}
+
+void sto_group_destroy(sto_group* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->hs[0]->stream);
+  free_group(g);
 }
 
 int sto_set_tableau(sto_handle* h, int32_t stages, const double* a, const double* b) {

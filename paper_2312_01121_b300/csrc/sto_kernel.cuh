@@ -732,6 +732,18 @@ struct AdjointProgram {
   }
 };
 
+// Row block and offset of row k in the tiled layout of a plan with G CTAs.
+__device__ __forceinline__ void tiled_row(int N, int G, int k, int* r0, int* R) {
+  const int q = N / G, rem = N % G;
+  if (k < rem * (q + 1)) {
+    *r0 = (k / (q + 1)) * (q + 1);
+    *R = q + 1;
+  } else {
+    *r0 = ((k - rem * (q + 1)) / q) * q + rem * (q + 1);
+    *R = q;
+  }
+}
+
 // ------------------------------------------------------------ the stepper
 
 // Per-row partial sums of W x for the rows a consumer warp owns (rows warp,
@@ -878,11 +890,13 @@ struct RowSums<kWf64, RPW> {
 // per panel).  kRowMajorW = true: a.W is the caller's row-major N x N matrix
 // (N a multiple of 4); each panel arrives as one bulk copy per row, issued by
 // the 32 lanes of the producer warp.  Consumers are identical in both.
-template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32>
-__global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
+//
+// stepper_engine is the whole launch as seen by CTA c of the G CTAs that
+// run reservoir `a`: sto_persistent_kernel runs one reservoir on the whole
+// grid, sto_group_kernel runs several, each on its own range of CTAs.
+template <int RPW, bool kRowMajorW, int kProg, int kW>
+__device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, const int G) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int c = blockIdx.x;
-  const int G = gridDim.x;
   const int q = a.N / G, rem = a.N % G;
   const int R = q + (c < rem ? 1 : 0);
   const int r0 = c * q + (c < rem ? c : rem);
@@ -1160,6 +1174,66 @@ __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __gri
   if (!aborted && owner) prog.finish(a, node);
 }
 
+template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32>
+__global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
+  stepper_engine<RPW, kRowMajorW, kProg, kW>(a, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+}
+
+// Several reservoirs with their own W in one cooperative launch.  The grid
+// is cut into n_lanes lanes of lane_width CTAs; lane l runs the reservoirs
+// order[lane_begin[l] .. lane_begin[l+1]) one after another, each on all of
+// the lane's CTAs (its record jobs[j] planned for that CTA count), so
+// reservoirs on different lanes run at the same time.  A lane's CTAs leave a
+// reservoir within one stage of each other and start the next together, so
+// every wait of the engine stays as short as in a lone launch; no CTA ever
+// waits for a CTA of another lane.
+struct GroupArgs {
+  const KArgs* jobs;      // per reservoir: the arguments of its stepper launch
+  const int* lane_begin;  // n_lanes + 1 offsets into order
+  const int* order;       // reservoir indices, lane by lane, in running order
+  const int* rpw;         // per reservoir: rows per consumer warp of its plan (1, 2, 4 or 8)
+  int n_lanes, lane_width;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) sto_group_kernel(const __grid_constant__ GroupArgs g) {
+  const int lane = static_cast<int>(blockIdx.x) / g.lane_width;
+  if (lane >= g.n_lanes) return;
+  const int c = static_cast<int>(blockIdx.x) - lane * g.lane_width;
+  for (int i = g.lane_begin[lane]; i < g.lane_begin[lane + 1]; ++i) {
+    const int j = g.order[i];
+    const KArgs& a = g.jobs[j];
+    switch (g.rpw[j]) {
+      case 1: stepper_engine<1, false, kProgForward, kWf32>(a, c, g.lane_width); break;
+      case 2: stepper_engine<2, false, kProgForward, kWf32>(a, c, g.lane_width); break;
+      case 4: stepper_engine<4, false, kProgForward, kWf32>(a, c, g.lane_width); break;
+      default: stepper_engine<8, false, kProgForward, kWf32>(a, c, g.lane_width); break;
+    }
+    // every warp has left the reservoir (the producer after draining its
+    // copies) before the next one re-initialises shared memory
+    __syncthreads();
+  }
+}
+
+// Re-tile W from the layout of a plan with G_old CTAs to one with G_new
+// (same panel count P).  The destination must be zeroed beforehand.
+__global__ void retile_w_kernel(const float* __restrict__ Wt_old, float* __restrict__ Wt_new, int N, int P,
+                                int G_old, int G_new) {
+  const long long total = static_cast<long long>(N) * P * kPanelCols;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(idx / (static_cast<long long>(P) * kPanelCols));
+    const int i = static_cast<int>(idx % (static_cast<long long>(P) * kPanelCols));  // padded column
+    int r0, R, s0, S0;
+    tiled_row(N, G_old, k, &r0, &R);
+    tiled_row(N, G_new, k, &s0, &S0);
+    const int j = i / kPanelCols, col = i % kPanelCols;
+    Wt_new[static_cast<size_t>(s0) * P * kPanelCols + static_cast<size_t>(j) * S0 * kPanelCols +
+           static_cast<size_t>(k - s0) * kPanelCols + col] =
+        Wt_old[static_cast<size_t>(r0) * P * kPanelCols + static_cast<size_t>(j) * R * kPanelCols +
+               static_cast<size_t>(k - r0) * kPanelCols + col];
+  }
+}
+
 // Scatter a row-major N x N matrix into the tiled layout: CTA c's rows
 // [r0, r0 + R) become P panels of R x kPanelCols floats, panel j holding
 // columns [j*kPanelCols, (j+1)*kPanelCols) (zero beyond N).  The destination
@@ -1218,18 +1292,6 @@ __global__ void tile_w_wide_kernel(const double* __restrict__ W, float* __restri
     } else {
       reinterpret_cast<double*>(dst)[0] = w;
     }
-  }
-}
-
-// Row block and offset of row k in the tiled layout of a plan with G CTAs.
-__device__ __forceinline__ void tiled_row(int N, int G, int k, int* r0, int* R) {
-  const int q = N / G, rem = N % G;
-  if (k < rem * (q + 1)) {
-    *r0 = (k / (q + 1)) * (q + 1);
-    *R = q + 1;
-  } else {
-    *r0 = ((k - rem * (q + 1)) / q) * q + rem * (q + 1);
-    *R = q;
   }
 }
 

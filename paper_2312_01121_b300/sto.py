@@ -111,6 +111,10 @@ SIGNATURES = {
     "sto_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(sto_batch_plan)]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "sto_group_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, ctypes.POINTER(_VP)]),
+    "sto_group_run": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(_VP)]),
+    "sto_group_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "sto_group_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -320,6 +324,59 @@ def sto_run_group(reservoirs, u, T=None, states_out=None):
             keep.append(k)
         outs = (_VP * n)(*ptrs)
     _check(load_library().sto_run_group(hs, n, pu, T, outs))
+
+
+class Group:
+    """Reservoirs with their own W advanced by one persistent launch per call
+    (lanes of CTAs run members side by side; see sto_group_create)."""
+
+    def __init__(self, reservoirs, lanes: int = 0):
+        self.reservoirs = list(reservoirs)  # keeps the handles alive
+        n = len(self.reservoirs)
+        hs = (_VP * n)(*[r.handle for r in self.reservoirs])
+        g = _VP()
+        _check(load_library().sto_group_create(hs, n, int(lanes), ctypes.byref(g)))
+        self.handle = g.value
+
+    def run(self, u, T=None, states_out=None):
+        if T is None:
+            T = int(u.shape[0])
+        n = len(self.reservoirs)
+        pu, ku = _ptr(u, np.float32)
+        keep = []
+        outs = None
+        if states_out is not None:
+            ptrs = []
+            for so in states_out:
+                p, k = _ptr(so, np.float32)
+                ptrs.append(p)
+                keep.append(k)
+            outs = (_VP * n)(*ptrs)
+        _check(load_library().sto_group_run(self.handle, pu, T, outs))
+
+    def info(self) -> dict:
+        n = len(self.reservoirs)
+        lanes, width = ctypes.c_int32(), ctypes.c_int32()
+        lane_of = (ctypes.c_int32 * n)()
+        _check(load_library().sto_group_get_info(self.handle, ctypes.byref(lanes), ctypes.byref(width), lane_of))
+        return {"lanes": lanes.value, "lane_width": width.value, "lane_of": list(lane_of)}
+
+    def close(self):
+        if self.handle:
+            load_library().sto_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def sto_get_info(h) -> dict:

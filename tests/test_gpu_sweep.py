@@ -220,3 +220,81 @@ def test_sweep_two_groups_bitwise_equal_to_one(sto, N, R, tile_n, slots):
             out.append((st, sw.state()))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def _own_w_members(sto, Ns, T, seed0=40):
+    systems = [make_system(N, "gauss", seed=seed0 + i, T=T) for i, N in enumerate(Ns)]
+    params = [sto.Params(substeps=3 + (i % 3), current=1e-3 + 3e-4 * i, A_cp=30.0) for i in range(len(Ns))]
+    return systems, params
+
+
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4])
+def test_group_single_launch_matches_separate_runs(sto, lanes):
+    """One persistent launch for reservoirs of uneven N and their own W and
+    substeps: every member's samples and final state are the bits of its own
+    sto_run under the same launch plan (grid = the lane width), over two
+    consecutive calls, whatever the lane count; one member also against the
+    oracle."""
+    Ns = [100, 333, 1000, 2049, 4000, 150, 777]
+    T = 2
+    u = make_system(4, "gauss", seed=1, T=2 * T)[3]
+    systems, params = _own_w_members(sto, Ns, 2 * T)
+    if lanes == 1:  # one lane of 148 CTAs: every member needs N >= 148
+        Ns, systems, params = Ns[1:5], systems[1:5], params[1:5]
+    grp_res = [sto.Reservoir(W, w_in, P, m0=m0) for (W, w_in, m0, _), P in zip(systems, params)]
+    outs = [np.zeros((2 * T, N), np.float32) for N in Ns]
+    with sto.Group(grp_res, lanes=lanes) as grp:
+        info = grp.info()
+        if lanes:
+            assert info["lanes"] == lanes
+        assert info["lanes"] * info["lane_width"] <= torch.cuda.get_device_properties(0).multi_processor_count
+        assert sorted(set(info["lane_of"])) == list(range(info["lanes"]))
+        grp.run(u[:T], T, [o[:T] for o in outs])
+        grp.run(u[T:], T, [o[T:] for o in outs])
+        ends = [r.state() for r in grp_res]
+    for r in grp_res:
+        r.close()
+    for (W, w_in, m0, _), P, o, e in zip(systems, params, outs, ends):
+        ref = np.zeros_like(o)
+        with sto.Reservoir(W, w_in, P, m0=m0, grid=info["lane_width"]) as r:
+            r.run(u[:T], ref[:T])
+            r.run(u[T:], ref[T:])
+            assert np.array_equal(r.state(), e)
+        assert np.array_equal(o, ref)
+    W, w_in, m0, _ = systems[0]
+    _, orc = oracle.run(oracle_params(params[0]), W.astype(np.float64), w_in.astype(np.float64),
+                        m0.astype(np.float64), u.astype(np.float64))
+    assert np.max(np.abs(outs[0] - orc)) <= 1e-5
+
+
+def test_group_device_buffers_and_rejections(sto):
+    Ns = [200, 300]
+    T = 2
+    u = make_system(4, "gauss", seed=2, T=T)[3]
+    systems, params = _own_w_members(sto, Ns, T, seed0=60)
+    res = [sto.Reservoir(W, w_in, P, m0=m0) for (W, w_in, m0, _), P in zip(systems, params)]
+    dev = torch.device("cuda")
+    outs = [torch.zeros((T, N), dtype=torch.float32, device=dev) for N in Ns]
+    with sto.Group(res) as grp:
+        width = grp.info()["lane_width"]
+        grp.run(torch.from_numpy(u).to(dev), T, outs)
+        torch.cuda.synchronize()
+        res[1].set_tableau([[0.0, 0.0], [1.0, 0.0]], [0.5, 0.5])  # not classic RK4 any more
+        with pytest.raises(sto.StoError) as e:
+            grp.run(u, T)
+        assert e.value.code == sto.STO_ENOTSUP
+    for (W, w_in, m0, _), P, o in zip(systems, params, outs):
+        ref = np.zeros((T, W.shape[0]), np.float32)
+        with sto.Reservoir(W, w_in, P, m0=m0, grid=width) as r:
+            r.run(u, ref)
+        assert np.array_equal(o.cpu().numpy(), ref)
+    with pytest.raises(sto.StoError) as e:
+        sto.Group([res[0], res[0]])
+    assert e.value.code == sto.STO_EINVAL
+    W64 = systems[0][0].astype(np.float64)
+    with sto.Reservoir(W64, systems[0][1], params[0], coupling="df64") as r64:
+        with pytest.raises(sto.StoError) as e:
+            sto.Group([res[0], r64])
+        assert e.value.code == sto.STO_ENOTSUP
+    for r in res:
+        r.close()
