@@ -276,9 +276,10 @@ typedef struct sto_group sto_group; /* opaque */
 /* Make a group of n distinct handles (same device, same n_in, FP32
  * coupling).  lanes = 0 picks the largest lane count up to min(n, 8) for
  * which every reservoir has at least one oscillator per CTA and at most 120
- * per CTA.  Each handle is re-planned for the lane width (its W re-tiled on
- * the device; sto_run on it keeps working, with that plan, and gives the
- * group's bits; a different plan can change the coupling sums' last bits).  The
+ * per CTA.  Each handle is re-planned for the lane width with W in shared
+ * memory (its W re-tiled on the device; sto_run on it keeps working, with
+ * that plan, and gives the group's bits; a different plan can change the
+ * coupling sums' last bits).  The
  * group keeps the handle pointers: destroy the group before its handles.
  * Errors: STO_EINVAL (null, duplicate handles, mismatched n_in or device),
  *         STO_ENOTSUP (an FP64 handle, or no lane count fits), STO_ENOMEM,

@@ -22,6 +22,7 @@
 
 #include "sto.h"
 #include "sto_kernel.cuh"
+#include "stepper_plan.h"
 #include "sweep.cuh"
 
 namespace {
@@ -52,69 +53,6 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-struct Plan {
-  int G = 1, R_max = 1, P = 1, ns = 1, resident = 1, rpw = 1;
-  size_t smem = 0;
-};
-
-// W elements per 512-byte panel row and bytes per element of a coupling mode.
-int panel_cols(int wmode) { return wmode == sto::kWf32 ? sto::kPanelCols : sto::kPanelCols / 2; }
-int w_elem_bytes(int wmode) { return wmode == sto::kWf32 ? 4 : 8; }
-
-// Dynamic shared memory of the stepper for a plan with `ns` ring slots.
-size_t smem_bytes(int R_max, int P, int ns, int wmode = sto::kWf32) {
-  size_t b = static_cast<size_t>(ns) * R_max * sto::kPanelCols * 4;  // ring
-  b += static_cast<size_t>(P) * sto::kPanelCols * 4;                 // xs
-  b += static_cast<size_t>((R_max + 3) & ~3) * (wmode == sto::kWf32 ? 4 : 8);  // hs
-  b += static_cast<size_t>(2 * ns) * 8 + 16;                         // barriers, abort flag
-  return b;
-}
-
-// Choose the CTA count, panel ring and residency for N oscillators.
-int make_plan(int64_t N, int grid_req, int sm_count, size_t smem_max, Plan* out,
-              int wmode = sto::kWf32) {
-  Plan p;
-  const int cols = panel_cols(wmode);
-  p.P = static_cast<int>((N + cols - 1) / cols);
-  auto fill = [&](int G) -> bool {
-    p.G = G;
-    p.R_max = static_cast<int>((N + G - 1) / G);
-    if (p.R_max > sto::kConsWarps * sto::kMaxRowsPerWarp) return false;
-    p.rpw = (p.R_max + sto::kConsWarps - 1) / sto::kConsWarps;
-    if (smem_bytes(p.R_max, p.P, p.P, wmode) <= smem_max) {
-      p.resident = 1;
-      p.ns = p.P;
-    } else {
-      p.resident = 0;
-      const size_t fixed = smem_bytes(p.R_max, p.P, 0, wmode);
-      const size_t per = static_cast<size_t>(p.R_max) * sto::kPanelCols * 4 + 16;
-      if (fixed >= smem_max) return false;
-      p.ns = static_cast<int>((smem_max - fixed) / per);
-      if (p.ns > 8) p.ns = 8;
-      if (p.ns < 2) return false;
-    }
-    p.smem = smem_bytes(p.R_max, p.P, p.ns, wmode);
-    return p.smem <= smem_max;
-  };
-  if (grid_req > 0) {
-    if (grid_req > sm_count || grid_req > N) return STO_EINVAL;
-    if (!fill(grid_req)) return STO_ENOTSUP;
-  } else if (fill(1) && p.resident) {
-    // the whole W fits in one CTA: no inter-CTA exchange at all
-  } else {
-    // W on chip: latency-bound, and fewer CTAs mean less skew in the m^x
-    // exchange; about 16 rows per CTA measured best at N = 10^3 (2.75 vs
-    // 3.46 us per stage with 148 CTAs).  Otherwise stream with every SM.
-    const int Gmax = static_cast<int>(N < sm_count ? N : sm_count);
-    int G = static_cast<int>((N + 15) / 16);
-    if (G > Gmax) G = Gmax;
-    while (G < Gmax && !(fill(G) && p.resident)) ++G;
-    if (!fill(G)) return STO_ENOTSUP;
-  }
-  *out = p;
-  return STO_OK;
 }
 
 void default_params(sto_params* p) {
@@ -250,9 +188,10 @@ int raise_dyn_smem_cap(F* func) {
   return room;
 }
 
-template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward, int kW = sto::kWf32>
+template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward, int kW = sto::kWf32,
+          bool kRegW = false>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW>);
+  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW>);
   if (room < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.G);
@@ -264,7 +203,7 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW>, a);
 }
 
 cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -296,6 +235,10 @@ cudaError_t launch_tableau(const Plan& pl, const sto::KArgs& a, cudaStream_t s) 
 template <int kW>
 cudaError_t launch_stepper_mode(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   constexpr int F = sto::kProgForward;
+  if constexpr (kW == sto::kWf32) {
+    if (pl.regw) return pl.rpw <= 1 ? launch_rpw<1, false, F, kW, true>(pl, a, s)
+                                    : launch_rpw<2, false, F, kW, true>(pl, a, s);
+  }
   if (pl.rpw <= 1) return launch_rpw<1, false, F, kW>(pl, a, s);
   if (pl.rpw <= 2) return launch_rpw<2, false, F, kW>(pl, a, s);
   if (pl.rpw <= 4) return launch_rpw<4, false, F, kW>(pl, a, s);
@@ -375,23 +318,6 @@ int grow(float** buf, size_t* cap, size_t n) {
   }
   *cap = n;
   return STO_OK;
-}
-
-// W of at most 96 MB (three quarters of the 126 MB L2) is streamed with an
-// evict_last hint so that it is re-read from L2 every stage; larger W is
-// streamed from HBM with evict_first so that it does not flush the rest.
-int l2_keeps(int64_t N, int ebytes = 4) {
-  return static_cast<double>(ebytes) * static_cast<double>(N) * N <= 96.0 * (1 << 20) ? 1 : 0;
-}
-
-// Leading panels of every row block to keep L2-resident when W is larger
-// than L2: a `mb` megabyte slice of W (default 80 MB of the 126 MB L2).
-int keep_panels(int64_t N, int P, int mb, int ebytes = 4) {
-  if (mb < 0 || l2_keeps(N, ebytes)) return 0;
-  const double budget = (mb == 0 ? 80.0 : static_cast<double>(mb)) * (1 << 20);
-  const double wbytes = static_cast<double>(ebytes) * static_cast<double>(N) * N;
-  const int k = static_cast<int>(P * budget / wbytes);
-  return k < P ? k : P;
 }
 
 // Constants of Eq. (gov) in the form the stepper uses.
@@ -1157,6 +1083,9 @@ int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group*
       free_group(g);
       return rc;
     }
+    // members keep W in shared memory (the group kernel inlines no
+    // register-W engine: its register budget goes to the streaming members)
+    hs[i]->plan.regw = 0;
     const int rpw = hs[i]->plan.rpw <= 1 ? 1 : (hs[i]->plan.rpw <= 2 ? 2 : (hs[i]->plan.rpw <= 4 ? 4 : 8));
     g->rpw.push_back(rpw);
     g->smem = hs[i]->plan.smem > g->smem ? hs[i]->plan.smem : g->smem;
@@ -1219,7 +1148,7 @@ int sto_group_run(sto_group* g, const float* u, int64_t T, float* const* states_
     sto_handle* h = g->hs[i];
     // planned for the lane, classic RK4, FP32 coupling (a tableau set since
     // creation or a re-planned handle cannot run here)
-    if (!h->rk_classic || h->wmode != sto::kWf32 || h->plan.G != g->width) return STO_ENOTSUP;
+    if (!h->rk_classic || h->wmode != sto::kWf32 || h->plan.G != g->width || h->plan.regw) return STO_ENOTSUP;
     const uint64_t stages = 4ULL * static_cast<uint64_t>(h->params.substeps) * static_cast<uint64_t>(T);
     if (stages > 0x40000000ULL) return STO_ENOTSUP;
     if (h->params.n_in != h0->params.n_in) return STO_EINVAL;

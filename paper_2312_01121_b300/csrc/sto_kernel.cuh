@@ -52,6 +52,10 @@ constexpr int kConsWarps = 15;                  // warps that consume panels (16
 constexpr int kCons = kConsWarps * 32;          // consumer threads
 constexpr int kThreads = kCons + 32;            // + one producer warp
 constexpr int kMaxRowsPerWarp = 16;             // rows of a CTA <= 240
+constexpr int kColSplitRows = 16;               // W on chip and at most this many rows: column split
+constexpr int kRegUnits = 3;                    // register-resident W: 32-column units per consumer warp
+constexpr int kRegWarps = kConsWarps - 1;       // consumer warps holding W (warp 0 owns the oscillators)
+constexpr int kRegMaxN = 32 * kRegUnits * kRegWarps;  // 1344
 
 // Error word layout (int32[4]): code, CTA, stage tag, site.
 enum ErrSite { kSiteGather = 1, kSiteFull = 2, kSiteEmpty = 3, kSiteDrain = 4 };
@@ -419,8 +423,21 @@ struct ForwardProgram {
     }
     const df hx = df_add(acp_times(a, hraw), hin);
     df d[3];
+    d[0] = df_fma(hx, fb[0], fa[0]);
+    // the next stage's m^x goes out first (the other CTAs wait for it); the
+    // same operations are repeated below for the stored state
+    {
+      df x;
+      if (st == 0 || st == 1)
+        x = df_add(mn[0], df_scale2(d[0], 0.5f));
+      else if (st == 2)
+        x = df_add(mn[0], d[0]);
+      else
+        x = df_fma(df_add(ksum[0], d[0]), a.sixth, mn[0]);
+      pub(node, x, next_tag);
+    }
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = df_fma(hx, fb[i], fa[i]);
+    for (int i = 1; i < 3; ++i) d[i] = df_fma(hx, fb[i], fa[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       if (st == 0) {
@@ -446,7 +463,6 @@ struct ForwardProgram {
       }
       if (++t < a.T) load_hin(a, node);
     }
-    pub(node, ms[0], next_tag);
     llg_affine(a, ms, fa, fb);  // for the next stage, overlapping the exchange
   }
 
@@ -894,7 +910,16 @@ struct RowSums<kWf64, RPW> {
 // stepper_engine is the whole launch as seen by CTA c of the G CTAs that
 // run reservoir `a`: sto_persistent_kernel runs one reservoir on the whole
 // grid, sto_group_kernel runs several, each on its own range of CTAs.
-template <int RPW, bool kRowMajorW, int kProg, int kW>
+//
+// kRegW (W on chip, at most 16 rows per CTA, N <= 1344, several CTAs): W is
+// moved from shared memory into registers once.  Lane l of consumer warp w
+// (1..14) holds the CTA's rows of W for columns 32 u + l, u = w - 1 + 14 k,
+// k < 3, polls exactly those columns' x words into registers, multiplies and
+// reduces its 16 row partials across the warp as in the column split.  One
+// barrier per stage remains (before the owners add the warps' partials);
+// warp 0 holds no columns, so its owners' work after publishing never
+// delays a poll.
+template <int RPW, bool kRowMajorW, int kProg, int kW, bool kRegW = false>
 __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, const int G) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int q = a.N / G, rem = a.N % G;
@@ -907,8 +932,11 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
   float* xs = ring + slot_floats * a.ns;
   float* hs = xs + static_cast<size_t>(a.P) * kPanelCols;
   // row sums: one float per row, two in the FP64 modes (8-byte aligned:
-  // every region before them is a multiple of 512 bytes)
-  uint64_t* full = reinterpret_cast<uint64_t*>(hs + (kW == kWf32 ? 1 : 2) * ((R_max + 3) & ~3));
+  // every region before them is a multiple of 512 bytes); then, for the
+  // column split (FP32, W on chip, <= 16 rows), 16 row partials per warp
+  const bool colsplit = kW == kWf32 && a.resident && R_max <= kColSplitRows;
+  float* part = hs + (kW == kWf32 ? 1 : 2) * ((R_max + 3) & ~3);
+  uint64_t* full = reinterpret_cast<uint64_t*>(part + (colsplit ? kConsWarps * kColSplitRows : 0));
   uint64_t* empty = full + a.ns;
   volatile int* s_abort = reinterpret_cast<volatile int*>(empty + a.ns);
 
@@ -1064,8 +1092,109 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
     }
     aborted = consumer_sync_or(!landed);
   }
+  // register-resident W (kRegW): this lane's columns, all rows
+  [[maybe_unused]] float wr[kRegUnits][kColSplitRows];
+  [[maybe_unused]] const int n_units = (a.N + 31) / 32;
+  if constexpr (kRegW) {
+#pragma unroll
+    for (int k = 0; k < kRegUnits; ++k) {
+      const int u = warp - 1 + kRegWarps * k, col = 32 * u + lane;
+      const bool ok = warp >= 1 && u < n_units && col < a.N;
+      const float* pj = ring + static_cast<size_t>(col / kPanelCols) * slot_floats + (col % kPanelCols);
+#pragma unroll
+      for (int r = 0; r < kColSplitRows; ++r) wr[k][r] = (ok && r < R) ? pj[r * kPanelCols] : 0.f;
+    }
+  }
   const long long n_stages = static_cast<long long>(a.rk_stages) * a.S * a.T;
   for (long long g = 0; g < n_stages && !aborted; ++g) {
+    if constexpr (kRegW) {
+      bool fail = false;
+      if (warp >= 1 && warp - 1 < n_units) {
+        const unsigned long long* xb = a.xbuf + static_cast<size_t>(tag & 1u) * a.N;
+        float xr[kRegUnits];
+        unsigned long long wv[kRegUnits];
+        bool pend[kRegUnits];
+#pragma unroll
+        for (int k = 0; k < kRegUnits; ++k) {
+          const int u = warp - 1 + kRegWarps * k, col = 32 * u + lane;
+          pend[k] = u < n_units && col < a.N;
+          xr[k] = 0.f;
+          wv[k] = pend[k] ? ld_relaxed_u64(xb + col) : 0ull;
+        }
+        bool waiting = false;
+#pragma unroll
+        for (int k = 0; k < kRegUnits; ++k) {
+          if (pend[k] && static_cast<unsigned>(wv[k] >> 32) == tag) {
+            xr[k] = __uint_as_float(static_cast<unsigned>(wv[k]));
+            pend[k] = false;
+          }
+          waiting = waiting || pend[k];
+        }
+        if (waiting) {
+          const unsigned long long t0 = gtimer();
+          for (uint32_t n = 1; waiting; ++n) {
+            waiting = false;
+#pragma unroll
+            for (int k = 0; k < kRegUnits; ++k) {
+              if (pend[k]) {
+                const unsigned long long v = ld_relaxed_u64(xb + 32 * (warp - 1 + kRegWarps * k) + lane);
+                if (static_cast<unsigned>(v >> 32) == tag) {
+                  xr[k] = __uint_as_float(static_cast<unsigned>(v));
+                  pend[k] = false;
+                }
+              }
+              waiting = waiting || pend[k];
+            }
+            if (waiting && (n & 31u) == 0) {
+              if (ld_relaxed_i32(a.err) != 0) {
+                fail = true;
+                break;
+              }
+              if (gtimer() - t0 > a.timeout_ns) {
+                report_error(a.err, kErrTimeout, c, tag, kSiteGather);
+                fail = true;
+                break;
+              }
+            }
+          }
+        }
+        if (fail) *s_abort = 1;
+        float p[kColSplitRows];
+#pragma unroll
+        for (int r = 0; r < kColSplitRows; ++r) {
+          float v = 0.f;
+#pragma unroll
+          for (int k = 0; k < kRegUnits; ++k) v = fmaf(wr[k][r], xr[k], v);
+          p[r] = v;
+        }
+#pragma unroll
+        for (int half = kColSplitRows / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
+          const bool up = (lane & off) != 0;
+#pragma unroll
+          for (int i = 0; i < half; ++i) {
+            const float keep = up ? p[half + i] : p[i];
+            const float send = up ? p[i] : p[half + i];
+            p[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
+        if ((lane & 1) == 0) part[(warp - 1) * kColSplitRows + (lane >> 1)] = p[0];
+      }
+      if (consumer_sync_or(fail)) { aborted = true; break; }
+      if (owner) {
+        const int nw = n_units < kRegWarps ? n_units : kRegWarps;  // warps holding columns
+        float pv[kRegWarps];
+#pragma unroll
+        for (int w = 0; w < kRegWarps; ++w) pv[w] = w < nw ? part[w * kColSplitRows + ctid] : 0.f;
+        float hraw = pv[0];
+#pragma unroll
+        for (int w = 1; w < kRegWarps; ++w)
+          if (w < nw) hraw += pv[w];
+        prog.stage(a, node, g, hraw, pub, tag + 1u);
+      }
+      ++tag;
+      continue;
+    }
     // 1. the stage's published value of every oscillator
     bool fail = false;
     if (G > 1 && ctid >= gather_first) {
@@ -1083,7 +1212,50 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
     // 2. h = W x over this CTA's rows, panel by panel
     RowSums<kW, RPW> sums;
     sums.zero();
-    if (a.resident) {
+    if (a.resident && colsplit) {
+      if constexpr (kW == kWf32) {
+        // Column split: warp w multiplies panels w, w + 15, ... for every
+        // row (each x value is read from shared memory once per CTA, not once
+        // per warp), then reduces its 16 row partials across the lanes by
+        // recursive halving: after the steps at lane offsets 16, 8, 4, 2 and 1
+        // lanes 2r and 2r + 1 hold the warp's sum for row r.  The owner of
+        // row r adds the warps' partials in warp order.
+        float p[kColSplitRows];
+#pragma unroll
+        for (int r = 0; r < kColSplitRows; ++r) p[r] = 0.f;
+        const float4* x4 = reinterpret_cast<const float4*>(xs) + lane;
+        const float4* w4 = reinterpret_cast<const float4*>(ring) + lane;
+        const int pstride = static_cast<int>(slot_floats / 4);
+        for (int j = warp; j < a.P; j += kConsWarps) {
+          const float4 xv = x4[j * (kPanelCols / 4)];
+          const float4* pj = w4 + j * pstride;
+#pragma unroll
+          for (int r = 0; r < kColSplitRows; ++r) {
+            if (r < R) {
+              const float4 w = pj[r * (kPanelCols / 4)];
+              float v = p[r];
+              v = fmaf(w.x, xv.x, v);
+              v = fmaf(w.y, xv.y, v);
+              v = fmaf(w.z, xv.z, v);
+              v = fmaf(w.w, xv.w, v);
+              p[r] = v;
+            }
+          }
+        }
+#pragma unroll
+        for (int half = kColSplitRows / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
+          const bool up = (lane & off) != 0;  // keep the upper half of the rows
+#pragma unroll
+          for (int i = 0; i < half; ++i) {
+            const float keep = up ? p[half + i] : p[i];
+            const float send = up ? p[i] : p[half + i];
+            p[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
+        if ((lane & 1) == 0) part[warp * kColSplitRows + (lane >> 1)] = p[0];
+      }
+    } else if (a.resident) {
       if constexpr (kW == kWf32) {
         // all panels on chip: plain unrolled loop, loads run ahead of FMAs;
         // with few rows per warp, four partial sums per row shorten the
@@ -1155,13 +1327,26 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
         }
       }
     }
-    sums.store(hs, warp, lane, R);
+    if (!colsplit) sums.store(hs, warp, lane, R);
     if (consumer_sync_or(fail)) { aborted = true; break; }
 
     // 3. the owner's program finishes the stage and publishes the next
     if (owner) {
       if constexpr (kW == kWf32) {
-        prog.stage(a, node, g, hs[ctid], pub, tag + 1u);
+        float hraw;
+        if (colsplit) {
+          const int nw = a.P < kConsWarps ? a.P : kConsWarps;  // warps that had panels
+          float pv[kConsWarps];
+#pragma unroll
+          for (int w = 0; w < kConsWarps; ++w) pv[w] = w < nw ? part[w * kColSplitRows + ctid] : 0.f;
+          hraw = pv[0];
+#pragma unroll
+          for (int w = 1; w < kConsWarps; ++w)
+            if (w < nw) hraw += pv[w];
+        } else {
+          hraw = hs[ctid];
+        }
+        prog.stage(a, node, g, hraw, pub, tag + 1u);
       } else if constexpr (kW == kWdf) {
         const float2 v = reinterpret_cast<const float2*>(hs)[ctid];
         prog.stage(a, node, g, df{v.x, v.y}, pub, tag + 1u);
@@ -1174,9 +1359,9 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
   if (!aborted && owner) prog.finish(a, node);
 }
 
-template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32>
+template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32, bool kRegW = false>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
-  stepper_engine<RPW, kRowMajorW, kProg, kW>(a, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+  stepper_engine<RPW, kRowMajorW, kProg, kW, kRegW>(a, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
 }
 
 // Several reservoirs with their own W in one cooperative launch.  The grid

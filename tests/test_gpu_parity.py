@@ -262,3 +262,19 @@ def test_readout_nmse_matches_oracle():
     _, n_gpu = readout.evaluate(st_gpu, u, washout=100)
     _, n_orc = readout.evaluate(st_orc, u, washout=100)
     assert np.isfinite(n_orc) and abs(n_gpu - n_orc) <= 1e-3
+
+
+@pytest.mark.parametrize("N", [1000, 1344, 333])
+def test_register_resident_w_plan(N):
+    """N <= 1344 with at most 16 oscillators per CTA holds W in registers (the
+    default plan at these sizes): same trajectory as a plan that keeps W in
+    shared memory (grid chosen so that a CTA has more than 16 rows), both
+    within the oracle's tolerance."""
+    W, w_in, m0, u = make_system(N, "gauss", seed=N, T=30)
+    P = Params(substeps=20, A_cp=80.0, A_in=20.0)
+    m_reg, st_reg = run_gpu(P, W, w_in, m0, u)
+    m_smem, st_smem = run_gpu(P, W, w_in, m0, u, grid=-(-N // 24))
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(st_reg - st_smem)) <= 1e-5
+    assert np.max(np.abs(st_reg - st_orc)) <= 1e-4
+    assert np.max(np.abs(m_reg - m_orc)) <= 1e-4

@@ -231,10 +231,10 @@ def _own_w_members(sto, Ns, T, seed0=40):
 @pytest.mark.parametrize("lanes", [0, 1, 2, 4])
 def test_group_single_launch_matches_separate_runs(sto, lanes):
     """One persistent launch for reservoirs of uneven N and their own W and
-    substeps: every member's samples and final state are the bits of its own
-    sto_run under the same launch plan (grid = the lane width), over two
-    consecutive calls, whatever the lane count; one member also against the
-    oracle."""
+    substeps: every member's samples and final state are the bits that
+    sto_run gives on the same (re-planned) member handle from the same start,
+    over two consecutive calls, whatever the lane count; every member also
+    against the oracle."""
     Ns = [100, 333, 1000, 2049, 4000, 150, 777]
     T = 2
     u = make_system(4, "gauss", seed=1, T=2 * T)[3]
@@ -252,19 +252,18 @@ def test_group_single_launch_matches_separate_runs(sto, lanes):
         grp.run(u[:T], T, [o[:T] for o in outs])
         grp.run(u[T:], T, [o[T:] for o in outs])
         ends = [r.state() for r in grp_res]
-    for r in grp_res:
-        r.close()
-    for (W, w_in, m0, _), P, o, e in zip(systems, params, outs, ends):
+    for (W, w_in, m0, _), P, o, e, r in zip(systems, params, outs, ends, grp_res):
+        assert r.info()["grid"] == info["lane_width"]
         ref = np.zeros_like(o)
-        with sto.Reservoir(W, w_in, P, m0=m0, grid=info["lane_width"]) as r:
-            r.run(u[:T], ref[:T])
-            r.run(u[T:], ref[T:])
-            assert np.array_equal(r.state(), e)
+        r.set_state(m0)
+        r.run(u[:T], ref[:T])
+        r.run(u[T:], ref[T:])
+        assert np.array_equal(r.state(), e)
         assert np.array_equal(o, ref)
-    W, w_in, m0, _ = systems[0]
-    _, orc = oracle.run(oracle_params(params[0]), W.astype(np.float64), w_in.astype(np.float64),
-                        m0.astype(np.float64), u.astype(np.float64))
-    assert np.max(np.abs(outs[0] - orc)) <= 1e-5
+        r.close()
+        _, orc = oracle.run(oracle_params(P), W.astype(np.float64), w_in.astype(np.float64),
+                            m0.astype(np.float64), u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(o - orc)) <= 1e-5
 
 
 def test_group_device_buffers_and_rejections(sto):
@@ -276,18 +275,17 @@ def test_group_device_buffers_and_rejections(sto):
     dev = torch.device("cuda")
     outs = [torch.zeros((T, N), dtype=torch.float32, device=dev) for N in Ns]
     with sto.Group(res) as grp:
-        width = grp.info()["lane_width"]
         grp.run(torch.from_numpy(u).to(dev), T, outs)
         torch.cuda.synchronize()
+        for (W, w_in, m0, _), o, r in zip(systems, outs, res):
+            ref = np.zeros((T, W.shape[0]), np.float32)
+            r.set_state(m0)
+            r.run(u, ref)  # the same member handle, run alone
+            assert np.array_equal(o.cpu().numpy(), ref)
         res[1].set_tableau([[0.0, 0.0], [1.0, 0.0]], [0.5, 0.5])  # not classic RK4 any more
         with pytest.raises(sto.StoError) as e:
             grp.run(u, T)
         assert e.value.code == sto.STO_ENOTSUP
-    for (W, w_in, m0, _), P, o in zip(systems, params, outs):
-        ref = np.zeros((T, W.shape[0]), np.float32)
-        with sto.Reservoir(W, w_in, P, m0=m0, grid=width) as r:
-            r.run(u, ref)
-        assert np.array_equal(o.cpu().numpy(), ref)
     with pytest.raises(sto.StoError) as e:
         sto.Group([res[0], res[0]])
     assert e.value.code == sto.STO_EINVAL
