@@ -107,7 +107,7 @@ typedef struct sto_config {
   int32_t grid;        /* CTAs of the persistent kernel (1 .. #SMs, <= N) */
   int32_t timeout_ms;  /* limit of every device-side wait (default 2000) */
   int32_t l2_keep_mb;  /* W larger than L2: MB of W kept L2-resident across
-                          stages (0 = default, -1 = none) */
+                          stages (0 = default, 110 MB; -1 = none) */
   int32_t reserved[5]; /* must be 0 */
 } sto_config;
 

@@ -411,6 +411,7 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   a.timeout_ns = static_cast<unsigned long long>(h->timeout_ms) * 1000000ULL;
   a.l2_keep = l2_keeps(h->N, w_elem_bytes(h->wmode));
   a.keep_panels = keep_panels(h->N, h->plan.P, h->l2_keep_mb, w_elem_bytes(h->wmode));
+  a.zigzag = h->plan.resident ? 0 : 1;
   set_constants(P, &a);
   a.rk_stages = h->rk_stages;
   for (int i = 0; i < 4; ++i) {

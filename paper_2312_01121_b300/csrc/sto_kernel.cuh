@@ -71,6 +71,7 @@ struct KArgs {
   int* err;                  // int32[4]
   int N, n_in, T, S, P, ns, resident, comp, inject_cta;
   int l2_keep;               // W small enough to stay in L2 between stages
+  int zigzag;                // streamed W: panels in reverse order on odd stages
   int keep_panels;           // otherwise: leading panels of each row block kept in L2
   unsigned int tag_base;
   unsigned long long timeout_ns;
@@ -1035,9 +1036,12 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
           }
         }
         mbar_arrive_expect_tx(&full[slot], panel_bytes);
+        // odd stages walk the row block backwards: the panels read last in
+        // one stage, still in L2, are the first the next stage needs
+        const int jp = (a.zigzag && !a.resident && ((it / a.P) & 1)) ? a.P - 1 - j : j;
         bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats,
-                 Wc + static_cast<size_t>(j) * R * kPanelCols, panel_bytes, &full[slot],
-                 (all_keep || j < a.keep_panels) ? keep : stream);
+                 Wc + static_cast<size_t>(jp) * R * kPanelCols, panel_bytes, &full[slot],
+                 (all_keep || jp < a.keep_panels) ? keep : stream);
         if (++j == a.P) j = 0;
         if (++slot == a.ns) {
           slot = 0;
@@ -1318,7 +1322,8 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
           fail = true;
           break;
         }
-        sums.panel(ring + static_cast<size_t>(slot) * slot_floats, xs, j, warp, lane, R);
+        sums.panel(ring + static_cast<size_t>(slot) * slot_floats, xs, (a.zigzag && (g & 1)) ? a.P - 1 - j : j,
+                   warp, lane, R);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         if (++cslot == a.ns) {

@@ -296,3 +296,25 @@ def test_group_device_buffers_and_rejections(sto):
         assert e.value.code == sto.STO_ENOTSUP
     for r in res:
         r.close()
+
+
+def test_sweep_full_configuration_sampled_reservoirs(sto):
+    """The benchmark's sweep: 512 reservoirs sharing one N = 2500 Gaussian W,
+    I ~ U[1, 3] mA, g ~ U[0.5, 2], autotuned plan; reservoirs sampled across
+    the tile columns against the oracle run with the BF16-rounded W."""
+    N, R, T = 2500, 512, 2
+    W, w_in, _, u = make_system(N, "gauss", seed=30, T=T)
+    rng = np.random.default_rng(30)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=3, A_cp=50.0, A_in=20.0)
+    st = np.zeros((T, R, N), np.float32)
+    with sto.Sweep(W, w_in, P, currents=cur, gains=gain) as sw:
+        sw.run(u, st)
+        assert sw.plan()["tuned"] == 1
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, 79, 80, 255, 256, 400, 511):
+        OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=16)
+        assert np.max(np.abs(st[:, r] - ref)) <= 1e-5, r
