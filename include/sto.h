@@ -370,11 +370,11 @@ typedef struct {
   int32_t reserved[2];
 } sto_batch_plan;
 
-/* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (3, 6 or 9:
- * three copy warps own every third slot; the state staging buffer is used
- * when it fits beside the ring), with one reservoir group, or (0, 0) to time
- * every candidate (tile_n in {16, 32, 40, 48, 64, ..., 128} up to R, slots
- * in {3, 6}, staging on and off, 1 and 2 groups) on two RK4 steps of zero
+/* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (3 to 9:
+ * three copy warps, warp p owning the slots s = p mod 3; the state staging
+ * buffer is used when it fits beside the ring), with one reservoir group, or
+ * (0, 0) to time every candidate (tile_n in {16, 32, 40, 48, 64, ..., 128} up
+ * to R, slots in {3, 4, 5, 6}, staging on and off, 1 and 2 groups) on two RK4 steps of zero
  * input from the batch's state (restored afterwards) and keep the fastest.
  * Tuned plans are cached per (device, N, R) for the life of the process.
  * The stage state is kept.

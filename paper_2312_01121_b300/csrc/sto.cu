@@ -1422,7 +1422,7 @@ void free_batch(sto_batch* b) {
 // two groups at least two tile columns.
 bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, SweepPlan* out) {
   if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < sto::kSpProducers || slots > sto::kSpMaxSlots ||
-      slots % sto::kSpProducers != 0 || groups < 1 || groups > 2)
+      groups < 1 || groups > 2)
     return false;
   SweepPlan p;
   p.bn = bn;
@@ -1540,7 +1540,7 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
 
 // Tile widths, ring depths and group counts the autotuner times.
 constexpr int kTuneBn[] = {16, 32, 40, 48, 64, 80, 96, 112, 128};
-constexpr int kTuneSlots[] = {3, 6};
+constexpr int kTuneSlots[] = {3, 4, 5, 6};
 constexpr int kTuneGroups[] = {1, 2};
 
 struct TuneKey {

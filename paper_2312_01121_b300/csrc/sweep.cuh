@@ -35,8 +35,10 @@
 // is a single contiguous block:
 //   Wt   tile (i, j) = rows [128 i, 128 i + 128) x columns [64 j, 64 j + 64)
 //        of W (BF16, zero padded), 16 KB at ((i * Kpad/64) + j) * 16 KB;
-//   Xt   tile (n, j) = reservoirs [BN n, BN n + BN) x columns [64 j, 64 j + 64)
-//        of [X_hi | X_lo] (K = 2 Kpad), BN * 128 B at ((n * 2Kpad/64) + j) * BN * 128 B;
+//   Xt   tile (n, j) = columns [64 j, 64 j + 64) of X_hi (rows 0 .. BN-1)
+//        and of X_lo (rows BN .. 2BN-1) for reservoirs [BN n, BN n + BN),
+//        2 BN * 128 B at ((n * Kpad/64) + j) * 2 BN * 128 B, so one copy
+//        brings both terms of a K slice;
 //   inside a tile: the 128-byte-swizzled K-major layout the tensor cores read
 //   at full shared-memory bandwidth: row r (64 K values = 128 B) at r * 128 B,
 //   its 16-byte chunk c (8 values) stored at chunk position c ^ (r % 8); 8-row
@@ -57,9 +59,8 @@ constexpr int kSwK = 64;           // K slice per copy
 constexpr int kSwSliceA = kSwM * kSwK * 2;             // 16 KB of W per slice
 constexpr int kSpEpiPerQuarter = 7;                    // epilogue warps per TMEM lane quarter
 constexpr int kSpEpiWarps = 4 * kSpEpiPerQuarter;      // 28
-// Copies issued by one thread complete one after another (about 0.4 us
-// each, however many are in flight), so three warps issue them, each owning
-// every third ring slot.
+// Three warps issue the copies, warp p owning the ring slots s = p (mod 3);
+// the ring holds 3 to 9 slots.
 constexpr int kSpProducers = 3;
 constexpr int kSpEpiFirst = 1 + kSpProducers;          // warp 0 multiplies, 1..3 copy
 constexpr int kSpThreads = 32 * (kSpEpiFirst + kSpEpiWarps);  // 1024
@@ -114,13 +115,16 @@ __host__ __device__ __forceinline__ size_t wt_offset(int row, int col, int Kpad)
   const size_t tile = static_cast<size_t>(row / kSwM) * (Kpad / kSwK) + col / kSwK;
   return tile * (kSwM * kSwK) + sw128_offset(row % kSwM, col % kSwK);
 }
+// kcol in [0, 2 Kpad): columns [0, Kpad) are X_hi, [Kpad, 2 Kpad) X_lo.
 __host__ __device__ __forceinline__ size_t xt_offset(int res, int kcol, int Kpad, int bn) {
-  const size_t tile = static_cast<size_t>(res / bn) * (2 * Kpad / kSwK) + kcol / kSwK;
-  return tile * (static_cast<size_t>(bn) * kSwK) + sw128_offset(res % bn, kcol % kSwK);
+  const int term = kcol >= Kpad ? 1 : 0, kk = kcol - term * Kpad;
+  const size_t tile = static_cast<size_t>(res / bn) * (Kpad / kSwK) + kk / kSwK;
+  return tile * (2 * static_cast<size_t>(bn) * kSwK) + sw128_offset(term * bn + res % bn, kk % kSwK);
 }
 
-// dt * dm/dt of Eq. (gov) for one oscillator in double-float, with the
-// reservoir's own H_s0 and the full x-field hx (coupling + input).
+// dt * dm/dt of Eq. (gov) for one oscillator in double-float (the damping
+// term's inner cross product in FP32), with the reservoir's own H_s0 and the
+// full x-field hx (coupling + input).
 __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df m[3], df hx,
                                                 df d[3]) {
   df s, pm[3];
@@ -130,10 +134,13 @@ __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df
                    df_fma(hs, pm[2], df_fma(c.hkp, m[2], c.happl))};
   const df t[3] = {df_cross1(m[1], b[2], m[2], b[1]), df_cross1(m[2], b[0], m[0], b[2]),
                    df_cross1(m[0], b[1], m[1], b[0])};
-  const df u[3] = {df_cross1(m[1], t[2], m[2], t[1]), df_cross1(m[2], t[0], m[0], t[2]),
-                   df_cross1(m[0], t[1], m[1], t[0])};
+  // the damping term m x (m x b) enters scaled by alpha = 0.005: formed in
+  // FP32 from the hi words, its rounding is ~3e-10 of the increment
+  const float uf[3] = {__fmaf_rn(m[1].hi, t[2].hi, -__fmul_rn(m[2].hi, t[1].hi)),
+                       __fmaf_rn(m[2].hi, t[0].hi, -__fmul_rn(m[0].hi, t[2].hi)),
+                       __fmaf_rn(m[0].hi, t[1].hi, -__fmul_rn(m[1].hi, t[0].hi))};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_fma(c.alpha, u[i], t[i]));
+  for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_add_f(t[i], __fmul_rn(c.alpha.hi, uf[i])));
 }
 
 // Finish stage st of pair (reservoir r, oscillator k) with the coupling sum
@@ -388,8 +395,8 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
   } else if (warp < kSpEpiFirst) {
     if (lane == 0) {
       // ------------------------------------------------------------ copies
-      // this warp owns positions P = pid (mod kSpProducers), hence ring
-      // slots P % slots = pid (mod kSpProducers): slots is a multiple of it
+      // this warp owns the ring slots s = pid (mod kSpProducers) and issues
+      // every position P that lands in one of them (s = P % slots)
       const int pid = warp - 1;
       const uint64_t pol = policy_evict_last();
       long long last = -1;  // last position issued
@@ -411,10 +418,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         const __nv_bfloat16* X = (g & 1) ? a.X1 : a.X0;
         const long long base = unit_base(g, q);
         const int L = n_my(q) * nk;
-        const int lp0 = static_cast<int>(((pid - base % kSpProducers) % kSpProducers + kSpProducers) % kSpProducers);
-        for (int lp = lp0; lp < L; lp += kSpProducers) {
+        for (int lp = 0; lp < L; ++lp) {
           const long long P = base + lp;
           const int s = static_cast<int>(P % a.slots);
+          if (s % kSpProducers != pid) continue;
           if (P >= a.slots &&
               !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((P / a.slots) - 1) & 1), a.timeout_ns,
                                  abort_flag)) {
@@ -425,12 +432,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           int tm, tn;
           sweep_tile(a, q, cta + i * G, &tm, &tn);
           unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
-          const __nv_bfloat16* xt = X + static_cast<size_t>(tn) * 2 * nk * (a.bn * kSwK);
+          const __nv_bfloat16* xt = X + (static_cast<size_t>(tn) * nk + j) * (2 * a.bn * kSwK);
           mbar_arrive_expect_tx(&full[s], slot_bytes);
           bulk_g2s(slot, a.Wb + (static_cast<size_t>(tm) * nk + j) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
-          bulk_g2s(slot + kSwSliceA, xt + static_cast<size_t>(j) * (a.bn * kSwK), sliceB, &full[s], pol);
-          bulk_g2s(slot + kSwSliceA + sliceB, xt + static_cast<size_t>(nk + j) * (a.bn * kSwK), sliceB,
-                   &full[s], pol);
+          bulk_g2s(slot + kSwSliceA, xt, 2 * sliceB, &full[s], pol);  // X_hi and X_lo rows
           last = P;
         }
       }
@@ -439,8 +444,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         s_abort = 1;
       }
       // never leave with copies in flight: the latest use of each own slot
-      for (long long P = last; P >= 0 && P > last - a.slots; P -= kSpProducers)
-        if (!mbar_wait_bounded(&full[P % a.slots], static_cast<uint32_t>((P / a.slots) & 1), a.timeout_ns, nullptr)) {
+      // (every own position up to `last` was issued, so it lies in (last - slots, last])
+      for (long long P = last; P >= 0 && P > last - a.slots; --P)
+        if (static_cast<int>(P % a.slots) % kSpProducers == pid &&
+            !mbar_wait_bounded(&full[P % a.slots], static_cast<uint32_t>((P / a.slots) & 1), a.timeout_ns, nullptr)) {
           report_error(a.err, kErrTimeout, cta, 0u, kSiteDrain);
           break;
         }
@@ -450,7 +457,8 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
     const int q4 = warp & 3;                      // TMEM lanes 32 q4 .. 32 q4 + 31
     const int wi = (warp - kSpEpiFirst) >> 2;     // 0 .. kSpEpiPerQuarter - 1
     const uint32_t lane_base = static_cast<uint32_t>(32 * q4) << 16;
-    const size_t lo_off = static_cast<size_t>(nk) * a.bn * kSwK;  // X_lo slices follow X_hi
+    // row jc + BN of a slice holds X_lo; BN % 8 == 0 keeps its swizzle phase
+    const size_t lo_off = static_cast<size_t>(a.bn) * kSwK;
     const size_t RN = static_cast<size_t>(a.R) * a.N;
     float2* stg = reinterpret_cast<float2*>(sp_smem + static_cast<size_t>(a.slots) * slot_bytes +
                                             static_cast<size_t>(warp - kSpEpiFirst) * kSpStageBytes);
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         const bool row_ok = k < static_cast<unsigned>(a.N);
         // X offset of (reservoir tn*bn + jcol, oscillator k), hi term: slice
         // base + sw128_offset(jcol, k % 64)
-        const size_t xk = (static_cast<size_t>(tn) * 2 * nk + (k >> 6)) * (a.bn * kSwK) + (k & 7u);
+        const size_t xk = (static_cast<size_t>(tn) * nk + (k >> 6)) * (2 * a.bn * kSwK) + (k & 7u);
         const unsigned kchunk = (k & 63u) >> 3;
         // input drive of oscillator k for this sample (the same for every reservoir)
         df drive{0.f, 0.f};
