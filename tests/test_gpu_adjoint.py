@@ -1,6 +1,8 @@
 """The hand-written adjoint (sto_adjoint) on the GPU: against the FP64
 oracle's adjoint, against finite differences of the GPU forward, invariance
 under the checkpoint interval, and the torch.autograd wrapper."""
+import os
+
 import numpy as np
 import pytest
 
@@ -136,3 +138,85 @@ def test_autograd_function_gives_readout_loss_gradients(sto):
     assert abs(A.grad.item() - ref["A_cp"]) <= 1e-3 * abs(ref["A_cp"])
     assert abs(I.grad.item() - ref["current"]) <= 1e-3 * abs(ref["current"])
     assert _rel(wt.grad.cpu().numpy(), ref["w_in"]) <= 1e-3
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_adjoint_full_configuration_n1000_t2000(sto):
+    """The benchmark's adjoint configuration: N = 1000, FP32, 2000 input
+    samples of 100 RK4 steps (2e5 RK4 steps), checkpoint every 100 samples.
+    (a) L = sum G * states with G ~ N(0, 1) over all samples: dA_cp, dI and
+        dw_in against the FP64 oracle's adjoint of the same run, stored in
+        tests/golden/adjoint_n1000_t2000.txt by make_adjoint_n1000_t2000.py
+        (30 minutes of host time), within 1e-3;
+    (b) the refitted ridge readout objective on y_t = u_{t-5} (washout 100)
+        gives the same gradients with another checkpoint interval;
+    (c) for G restricted to the first 1000 samples (the adjoint still sweeps
+        all 20 checkpoint segments), central differences of the GPU forward
+        within 1e-3: h = 1e-5 relative for A_cp, 1e-7 for I.
+    Over 2e5 steps the reservoir is weakly chaotic: sensitivities grow ~47x
+    from 1000 to 2000 samples, and differences of the FP32 forward over all
+    2000 samples do not settle below ~2e-3 at any step (the truncation error
+    needs h <= 1e-6, where the two perturbed runs' FP32 rounding, amplified
+    by the dynamics, takes over), hence the oracle for the full horizon and
+    differences over the first half."""
+    from paper_2312_01121_b300 import autograd as ag
+    N, T, washout, beta = 1000, 2000, 100, 1e-4
+    W, w_in, m0, u = make_system(N, "gauss", seed=21, T=T)
+    dev = torch.device("cuda")
+    P = sto.Params(substeps=100)
+    ud = torch.from_numpy(u).to(dev)
+    G = np.random.default_rng(21).standard_normal((T, N)).astype(np.float32)
+    gold = _golden("adjoint_n1000_t2000.txt")
+    with sto.Reservoir(W, w_in, P, m0=m0) as r:
+        g = r.adjoint(ud, torch.from_numpy(G).to(dev), ckpt_every=100, want_m0=False)
+        for name, key in (("A_cp", "dA_cp"), ("current", "dcurrent")):
+            assert abs(g[name] - gold[key]) <= 1e-3 * abs(gold[key]), (name, g[name], gold[key])
+        scale = np.max(np.abs(g["w_in"]))
+        for k in (0, 1, 499, 998):
+            assert abs(g["w_in"][k, 0] - gold[f"dw_in_{k}"]) <= 1e-3 * scale, k
+
+        y = torch.zeros(T, dtype=torch.float64, device=dev)
+        y[5:] = torch.from_numpy(u[:-5, 0]).to(dev, torch.float64)
+        grads = []
+        for K in (100, 250):
+            r.set_params(P)
+            r.set_input_weights(w_in)
+            r.set_state(m0)
+            A = torch.tensor(P.A_cp, dtype=torch.float64, requires_grad=True)
+            I = torch.tensor(P.current, dtype=torch.float64, requires_grad=True)
+            wt = torch.from_numpy(w_in.astype(np.float64)).to(dev).requires_grad_(True)
+            st = ag.sto_states(r, A, I, wt, ud, ckpt_every=K)
+            ag.ridge_objective(st, y, washout, beta).backward()
+            grads.append((A.grad.item(), I.grad.item(), wt.grad.cpu().numpy()))
+        assert abs(grads[0][0] - grads[1][0]) <= 1e-9 * abs(grads[0][0])
+        assert abs(grads[0][1] - grads[1][1]) <= 1e-9 * abs(grads[0][1])
+        assert np.max(np.abs(grads[0][2] - grads[1][2])) <= 1e-9 * np.max(np.abs(grads[0][2]))
+
+        G[1000:] = 0.0
+        Gd = torch.from_numpy(G).to(dev)
+        r.set_params(P)
+        r.set_input_weights(w_in)
+        r.set_state(m0)
+        g_half = r.adjoint(ud, Gd, ckpt_every=100, want_w_in=False, want_m0=False)
+
+        def L(params):
+            r.set_params(params)
+            r.set_input_weights(w_in)
+            r.set_state(m0)
+            st = torch.empty((T, N), dtype=torch.float32, device=dev)
+            r.run(ud, st)
+            return float((st.double() * Gd.double()).sum())
+
+        for name, rel in (("A_cp", 1e-5), ("current", 1e-7)):
+            h = rel * getattr(P, name)
+            fd = (L(P.replace(**{name: getattr(P, name) + h})) - L(P.replace(**{name: getattr(P, name) - h}))) / (2 * h)
+            assert abs(g_half[name] - fd) <= 1e-3 * abs(fd), (name, g_half[name], fd)
