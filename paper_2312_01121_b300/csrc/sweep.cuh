@@ -274,14 +274,11 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
   const int G0 = T0 < G ? T0 : G, G1 = T1 < G ? T1 : G;
   auto n_my = [&](int q) { return q == 0 ? my0 : my1; };
   const int nk = a.Kpad / kSwK;
-  const long long L0 = static_cast<long long>(my0) * nk, L1 = static_cast<long long>(my1) * nk;
   const uint32_t sliceB = static_cast<uint32_t>(a.bn) * kSwK * 2;  // one X slice (hi or lo)
   const uint32_t slot_bytes = kSwSliceA + 2 * sliceB;
   const long long n_stages = 4LL * a.S * a.T;
   const long long n_units = n_stages * n_grp;
   const volatile int* abort_flag = &s_abort;
-  // ring position of the first K slice of unit u = (g, q)
-  auto unit_base = [&](long long g, int q) -> long long { return g * (L0 + L1) + (q == 1 ? L0 : 0); };
 
   if (tid == 0) {
     for (int s = 0; s < a.slots; ++s) {
@@ -315,6 +312,11 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
       // ----------------------------------------- group barriers and MMAs
       const uint32_t idesc = umma_idesc_bf16(kSwM, 2 * a.bn);  // [X_hi | X_lo] rows
       long long seq = 0;  // accumulator sequence number of the unit's first tile
+      // ring slot and phase parity of the next position: positions run
+      // contiguously through all units, so both advance by counting (a 64-bit
+      // division by the ring depth per K slice cost more than its MMAs)
+      int s = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (long long u = 0; u < n_units && ok; ++u) {
         const long long g = u / n_grp;
@@ -343,44 +345,45 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           fence_proxy_async_global();
         }
         st_release_cta_u64(&s_go, static_cast<unsigned long long>(u + 1));  // the copy warps may read this unit's X
-        const long long base = unit_base(g, q);
-        const int L = nm * nk;
-        for (int lq = 0; lq < L; ++lq) {
-          const int i = lq / nk, j = lq % nk;
+        for (int i = 0; i < nm && ok; ++i) {
           const long long sq = seq + i;
-          const int b = static_cast<int>(sq & 1);
-          if (j == 0 && sq >= 2) {
-            // the epilogue has read this accumulator's previous tile
-            if (!mbar_wait_bounded(&acc_empty[b], static_cast<uint32_t>(((sq >> 1) - 1) & 1), a.timeout_ns,
-                                   abort_flag)) {
+          for (int j = 0; j < nk; ++j) {
+            const int b = static_cast<int>(sq & 1);
+            if (j == 0 && sq >= 2) {
+              // the epilogue has read this accumulator's previous tile
+              if (!mbar_wait_bounded(&acc_empty[b], static_cast<uint32_t>(((sq >> 1) - 1) & 1), a.timeout_ns,
+                                     abort_flag)) {
+                ok = false;
+                break;
+              }
+            }
+            if (!mbar_wait_bounded(&full[s], ph, a.timeout_ns, abort_flag)) {
               ok = false;
               break;
             }
-          }
-          const long long Q = base + lq;
-          const int s = static_cast<int>(Q % a.slots);
-          if (!mbar_wait_bounded(&full[s], static_cast<uint32_t>((Q / a.slots) & 1), a.timeout_ns, abort_flag)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = smem_u32(sp_smem + static_cast<size_t>(s) * slot_bytes);
-          const uint32_t b0 = a0 + kSwSliceA;
-          const uint32_t dt = tmem + static_cast<uint32_t>(b * a.acc_cols);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sp_smem + static_cast<size_t>(s) * slot_bytes);
+            const uint32_t b0 = a0 + kSwSliceA;
+            const uint32_t dt = tmem + static_cast<uint32_t>(b * a.acc_cols);
 #pragma unroll
-          for (int jk = 0; jk < kSwK / 16; ++jk) {
-            // B: the X_hi slice and the X_lo slice behind it, 2 bn rows
-            const uint64_t ad = umma_desc_sw128(a0 + jk * 32);
-            const uint64_t bd = umma_desc_sw128(b0 + jk * 32);
-            const uint32_t accum = (j > 0 || jk > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                : "memory");
+            for (int jk = 0; jk < kSwK / 16; ++jk) {
+              // B: the X_hi slice and the X_lo slice behind it, 2 bn rows
+              const uint64_t ad = umma_desc_sw128(a0 + jk * 32);
+              const uint64_t bd = umma_desc_sw128(b0 + jk * 32);
+              const uint32_t accum = (j > 0 || jk > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                  : "memory");
+            }
+            umma_commit(&empty[s]);
+            if (j == nk - 1) umma_commit(&acc_full[b]);
+            if (++s == a.slots) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
-          umma_commit(&empty[s]);
-          if (j == nk - 1) umma_commit(&acc_full[b]);
         }
         seq += nm;
       }
@@ -400,6 +403,11 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
       const int pid = warp - 1;
       const uint64_t pol = policy_evict_last();
       long long last = -1;  // last position issued
+      // position, its ring slot and that slot's phase parity, by counting
+      // (no 64-bit division by the ring depth per position)
+      long long P = 0;
+      int s = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (long long u = 0; u < n_units && ok; ++u) {
         if (ld_acquire_cta_u64(&s_go) <= static_cast<unsigned long long>(u)) {
@@ -416,27 +424,31 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         const long long g = u / n_grp;
         const int q = static_cast<int>(u % n_grp);
         const __nv_bfloat16* X = (g & 1) ? a.X1 : a.X0;
-        const long long base = unit_base(g, q);
-        const int L = n_my(q) * nk;
-        for (int lp = 0; lp < L; ++lp) {
-          const long long P = base + lp;
-          const int s = static_cast<int>(P % a.slots);
-          if (s % kSpProducers != pid) continue;
-          if (P >= a.slots &&
-              !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((P / a.slots) - 1) & 1), a.timeout_ns,
-                                 abort_flag)) {
-            ok = false;
-            break;
-          }
-          const int i = lp / nk, j = lp % nk;
+        const int nm = n_my(q);
+        for (int i = 0; i < nm && ok; ++i) {
           int tm, tn;
           sweep_tile(a, q, cta + i * G, &tm, &tn);
-          unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
-          const __nv_bfloat16* xt = X + (static_cast<size_t>(tn) * nk + j) * (2 * a.bn * kSwK);
-          mbar_arrive_expect_tx(&full[s], slot_bytes);
-          bulk_g2s(slot, a.Wb + (static_cast<size_t>(tm) * nk + j) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
-          bulk_g2s(slot + kSwSliceA, xt, 2 * sliceB, &full[s], pol);  // X_hi and X_lo rows
-          last = P;
+          const __nv_bfloat16* Wt = a.Wb + static_cast<size_t>(tm) * nk * (kSwM * kSwK);
+          const __nv_bfloat16* xt = X + static_cast<size_t>(tn) * nk * (2 * a.bn * kSwK);
+          for (int j = 0; j < nk; ++j, ++P) {
+            if (s % kSpProducers == pid) {
+              // the slot's previous use (lap - 1, parity ph ^ 1) has been consumed
+              if (P >= a.slots && !mbar_wait_bounded(&empty[s], ph ^ 1u, a.timeout_ns, abort_flag)) {
+                ok = false;
+                break;
+              }
+              unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
+              mbar_arrive_expect_tx(&full[s], slot_bytes);
+              bulk_g2s(slot, Wt + static_cast<size_t>(j) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
+              bulk_g2s(slot + kSwSliceA, xt + static_cast<size_t>(j) * (2 * a.bn * kSwK), 2 * sliceB, &full[s],
+                       pol);  // X_hi and X_lo rows
+              last = P;
+            }
+            if (++s == a.slots) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
         }
       }
       if (!ok) {
