@@ -1027,6 +1027,7 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
       long long it = 0;
       int slot = 0, j = 0;
       uint32_t lap = 0;  // it / ns
+      uint32_t odd = 0;  // (it / P) & 1: the stage walks its row block backwards
       bool ok = true;
       for (; it < total; ++it) {
         if (!a.resident && lap > 0) {
@@ -1038,11 +1039,14 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
         mbar_arrive_expect_tx(&full[slot], panel_bytes);
         // odd stages walk the row block backwards: the panels read last in
         // one stage, still in L2, are the first the next stage needs
-        const int jp = (a.zigzag && !a.resident && ((it / a.P) & 1)) ? a.P - 1 - j : j;
+        const int jp = (a.zigzag && !a.resident && odd) ? a.P - 1 - j : j;
         bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats,
                  Wc + static_cast<size_t>(jp) * R * kPanelCols, panel_bytes, &full[slot],
                  (all_keep || jp < a.keep_panels) ? keep : stream);
-        if (++j == a.P) j = 0;
+        if (++j == a.P) {
+          j = 0;
+          odd ^= 1u;
+        }
         if (++slot == a.ns) {
           slot = 0;
           ++lap;
