@@ -337,6 +337,7 @@ typedef struct sto_batch sto_batch; /* opaque */
  *   w_in        N x n_in float32 (host or device), shared.
  *   m0          R x 3 x N float32 initial states (reservoir-major; host or
  *               device) or NULL for Eq. (initial).
+ * Limits: N <= 32768, R <= 65536 and R N <= 2^29 (STO_ENOTSUP otherwise).
  * Errors: STO_EINVAL, STO_ENONFINITE, STO_ENOMEM, STO_ENOTSUP, STO_ECUDA. */
 STO_API int sto_batch_create(int64_t N, int32_t R, const sto_params* params,
                              const double* current, const double* input_gain,

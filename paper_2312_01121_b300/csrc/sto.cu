@@ -1688,7 +1688,8 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
   if (N < 1 || R < 1 || !W || !w_in) return STO_EINVAL;
   int rc = check_params(params);
   if (rc) return rc;
-  if (N > 32768 || R > 65536) return STO_ENOTSUP;
+  // the update indexes the [3][R][N] state with 32-bit offsets
+  if (N > 32768 || R > 65536 || static_cast<long long>(N) * R > (1LL << 29)) return STO_ENOTSUP;
   sto_batch* b = new (std::nothrow) sto_batch();
   if (!b) return STO_ENOMEM;
   b->stream = static_cast<cudaStream_t>(stream);

@@ -143,19 +143,20 @@ __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df
   for (int i = 0; i < 3; ++i) d[i] = df_mul(c.gdt, df_add_f(t[i], __fmul_rn(c.alpha.hi, uf[i])));
 }
 
-// Finish stage st of pair (reservoir r, oscillator k) with the coupling sum
-// hraw, given the pair's state (mn; ms and ks when st > 0) and the input
-// drive w_in . u_t of oscillator k: the RK4 combination, the next stage's X
-// (hi and lo BF16 terms, at element offsets xo and xo + lo_off of Xn) and the
-// sample at the end of an input sample.  Each stage writes only the state the
-// next one reads: stages 0-2 write (sum, stage state); stage 3 writes m_{n+1}
-// only (the next stage 0 starts from it).
-__device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsigned k, float hraw,
-                                           int st, int t, bool sample, df drive, df mn[3], df ms[3],
-                                           df ks[3], __nv_bfloat16* Xn, size_t xo, size_t lo_off) {
-  const size_t RN = static_cast<size_t>(a.R) * a.N;
-  const size_t idx = static_cast<size_t>(r) * a.N + k;
-  if (st == 0) {
+// Finish stage ST of pair (reservoir r, oscillator k; element idx = r N + k
+// of the [3][R][N] state arrays) with the coupling sum hraw, given the
+// pair's state (mn; ms and ks when ST > 0) and the input drive w_in . u_t of
+// oscillator k: the RK4 combination, the next stage's X (hi and lo BF16
+// terms, at element offsets xo and xo + lo_off of Xn) and the sample at the
+// end of an input sample.  Each stage writes only the state the next one
+// reads: stages 0-2 write (sum, stage state); stage 3 writes m_{n+1} only
+// (the next stage 0 starts from it).  Offsets are 32-bit: the batch keeps
+// R N <= 2^29, so 3 R N and the X extent stay below 2^31.
+template <int ST>
+__device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsigned idx, unsigned RN,
+                                           float hraw, int t, bool sample, df drive, df mn[3], df ms[3],
+                                           df ks[3], __nv_bfloat16* Xn, unsigned xo, unsigned lo_off) {
+  if constexpr (ST == 0) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) ms[i] = mn[i];
   }
@@ -164,13 +165,13 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
   sweep_increment(a.c, a.hs0_r[r], ms, hx, d);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    if (st == 0) {
+    if constexpr (ST == 0) {
       ks[i] = d[i];
       ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
-    } else if (st == 1) {
+    } else if constexpr (ST == 1) {
       ks[i] = df_add(ks[i], df_scale2(d[i], 2.0f));
       ms[i] = df_add(mn[i], df_scale2(d[i], 0.5f));
-    } else if (st == 2) {
+    } else if constexpr (ST == 2) {
       ks[i] = df_add(ks[i], df_scale2(d[i], 2.0f));
       ms[i] = df_add(mn[i], d[i]);
     } else {
@@ -181,7 +182,7 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    if (st == 3) {
+    if constexpr (ST == 3) {
       a.mn[i * RN + idx] = make_float2(mn[i].hi, mn[i].lo);
     } else {
       a.ms[i * RN + idx] = make_float2(ms[i].hi, ms[i].lo);
@@ -193,8 +194,9 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
   const __nv_bfloat16 xl = __float2bfloat16_rn(x - __bfloat162float(xh));
   Xn[xo] = xh;
   Xn[xo + lo_off] = xl;
-  if (st == 3 && sample && a.states_out)
-    a.states_out[static_cast<size_t>(t) * RN + idx] = mn[a.comp].hi;
+  if constexpr (ST == 3) {
+    if (sample && a.states_out) a.states_out[static_cast<size_t>(t) * RN + idx] = mn[a.comp].hi;
+  }
 }
 
 // Asynchronous 8-byte global -> shared copy (no register staging).
@@ -256,6 +258,83 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int q, int idx, i
 // passes each unit's group barrier, releases the unit to the copy warps and
 // issues the MMAs; warps 1-3 (one thread each) fill their ring slots; warps
 // 4-31 run the epilogue.
+// The epilogue of one tile for one epilogue warp: the pairs (reservoir
+// tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + 7, ...
+// The state of the next column's pair is copied into shared memory (stg)
+// while the current one is computed when STAGED.  tacc addresses this
+// warp's TMEM lanes of the accumulator; xk is the X offset of (jc = 0, k).
+// Returns false when the accumulator never filled (timeout or abort).
+template <int ST, bool STAGED>
+__device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, float2* stg, uint32_t tacc, int tn,
+                                                  unsigned k, bool row_ok, unsigned xk, unsigned kchunk,
+                                                  df drive, int t, bool sample, __nv_bfloat16* Xn,
+                                                  unsigned lo_off, int wi, int lane, uint64_t* acc_bar,
+                                                  uint32_t acc_parity, const volatile int* abort_flag) {
+  const unsigned R = static_cast<unsigned>(a.R), N = static_cast<unsigned>(a.N), RN = R * N;
+  constexpr unsigned kStep = kSpEpiPerQuarter;
+  const unsigned istep = kStep * N;
+  unsigned r = static_cast<unsigned>(tn * a.bn + wi), idx = r * N + k;
+  auto prefetch = [&](unsigned rr, unsigned ii) {
+    if (row_ok && rr < R) {
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq) {
+        cp_async8(stg + (qq * 32 + lane), a.mn + (qq * RN + ii));
+        if constexpr (ST > 0) {
+          cp_async8(stg + ((3 + qq) * 32 + lane), a.ms + (qq * RN + ii));
+          cp_async8(stg + ((6 + qq) * 32 + lane), a.ksum + (qq * RN + ii));
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (STAGED) prefetch(r, idx);  // overlaps the tile's MMAs
+  const bool landed = mbar_wait_bounded(acc_bar, acc_parity, a.timeout_ns, abort_flag);
+  if (!__all_sync(0xffffffffu, landed)) {
+    if constexpr (STAGED) cp_async_wait_all();
+    return false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  for (int jc = wi; jc < a.bn; jc += kStep, r += kStep, idx += istep) {
+    uint32_t vh, vl;  // W X_hi and W X_lo of this pair
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(vh) : "r"(tacc + jc));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(vl) : "r"(tacc + a.bn + jc));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const float hraw = __fadd_rn(__uint_as_float(vh), __uint_as_float(vl));
+    const bool pair_ok = row_ok && r < R;
+    df mn[3], ms[3], ks[3];
+    if constexpr (STAGED) {
+      cp_async_wait_all();
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq) {
+        const float2 x0 = stg[qq * 32 + lane];
+        mn[qq] = df{x0.x, x0.y};
+        if constexpr (ST > 0) {
+          const float2 x1 = stg[(3 + qq) * 32 + lane], x2 = stg[(6 + qq) * 32 + lane];
+          ms[qq] = df{x1.x, x1.y};
+          ks[qq] = df{x2.x, x2.y};
+        }
+      }
+      if (jc + static_cast<int>(kStep) < a.bn) prefetch(r + kStep, idx + istep);
+    } else if (pair_ok) {
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq) {
+        const float2 x0 = a.mn[qq * RN + idx];
+        mn[qq] = df{x0.x, x0.y};
+        if constexpr (ST > 0) {
+          const float2 x1 = a.ms[qq * RN + idx], x2 = a.ksum[qq * RN + idx];
+          ms[qq] = df{x1.x, x1.y};
+          ks[qq] = df{x2.x, x2.y};
+        }
+      }
+    }
+    if (pair_ok) {
+      const unsigned xo = xk + static_cast<unsigned>(jc) * 64u + ((kchunk ^ (static_cast<unsigned>(jc) & 7u)) << 3);
+      sweep_pair<ST>(a, r, idx, RN, hraw, t, sample, drive, mn, ms, ks, Xn, xo, lo_off);
+    }
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
   // the swizzle pattern repeats every 1024 B: the ring starts on such a boundary
@@ -470,8 +549,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
     const int wi = (warp - kSpEpiFirst) >> 2;     // 0 .. kSpEpiPerQuarter - 1
     const uint32_t lane_base = static_cast<uint32_t>(32 * q4) << 16;
     // row jc + BN of a slice holds X_lo; BN % 8 == 0 keeps its swizzle phase
-    const size_t lo_off = static_cast<size_t>(a.bn) * kSwK;
-    const size_t RN = static_cast<size_t>(a.R) * a.N;
+    const unsigned lo_off = static_cast<unsigned>(a.bn) * kSwK;
     float2* stg = reinterpret_cast<float2*>(sp_smem + static_cast<size_t>(a.slots) * slot_bytes +
                                             static_cast<size_t>(warp - kSpEpiFirst) * kSpStageBytes);
     long long seq = 0;
@@ -494,7 +572,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         const bool row_ok = k < static_cast<unsigned>(a.N);
         // X offset of (reservoir tn*bn + jcol, oscillator k), hi term: slice
         // base + sw128_offset(jcol, k % 64)
-        const size_t xk = (static_cast<size_t>(tn) * nk + (k >> 6)) * (2 * a.bn * kSwK) + (k & 7u);
+        const unsigned xk = (static_cast<unsigned>(tn) * nk + (k >> 6)) * (2u * a.bn * kSwK) + (k & 7u);
         const unsigned kchunk = (k & 63u) >> 3;
         // input drive of oscillator k for this sample (the same for every reservoir)
         df drive{0.f, 0.f};
@@ -504,76 +582,31 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
             drive = df_add(drive, two_prod(a.w_in[static_cast<size_t>(k) * a.n_in + jj],
                                            a.u[static_cast<size_t>(t) * a.n_in + jj]));
         }
-        // the state of the next column's pair is copied into shared memory
-        // while the current one is computed
-        auto prefetch = [&](int jc) {
-          if (!a.staged) return;
-          const unsigned r = static_cast<unsigned>(tn * a.bn + jc);
-          if (row_ok && r < static_cast<unsigned>(a.R)) {
-            const size_t idx = static_cast<size_t>(r) * a.N + k;
-#pragma unroll
-            for (int qq = 0; qq < 3; ++qq) {
-              cp_async8(stg + (qq * 32 + lane), a.mn + qq * RN + idx);
-              if (st > 0) {
-                cp_async8(stg + ((3 + qq) * 32 + lane), a.ms + qq * RN + idx);
-                cp_async8(stg + ((6 + qq) * 32 + lane), a.ksum + qq * RN + idx);
-              }
-            }
+        const uint32_t tacc = tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols);
+        const uint32_t par = static_cast<uint32_t>((seq >> 1) & 1);
+        bool landed = false;
+#define STO_SWEEP_TILE(ST_, STAGED_)                                                                    \
+  landed = sweep_tile_update<ST_, STAGED_>(a, stg, tacc, tn, k, row_ok, xk, kchunk, drive, t, sample, Xn, \
+                                           lo_off, wi, lane, &acc_full[b], par, abort_flag)
+        if (a.staged) {
+          switch (st) {
+            case 0: STO_SWEEP_TILE(0, true); break;
+            case 1: STO_SWEEP_TILE(1, true); break;
+            case 2: STO_SWEEP_TILE(2, true); break;
+            default: STO_SWEEP_TILE(3, true); break;
           }
-          cp_async_commit();
-        };
-        prefetch(wi);  // overlaps the tile's MMAs
-        const bool landed = mbar_wait_bounded(&acc_full[b], static_cast<uint32_t>((seq >> 1) & 1), a.timeout_ns,
-                                              abort_flag);
-        if (!__all_sync(0xffffffffu, landed)) {
-          cp_async_wait_all();
+        } else {
+          switch (st) {
+            case 0: STO_SWEEP_TILE(0, false); break;
+            case 1: STO_SWEEP_TILE(1, false); break;
+            case 2: STO_SWEEP_TILE(2, false); break;
+            default: STO_SWEEP_TILE(3, false); break;
+          }
+        }
+#undef STO_SWEEP_TILE
+        if (!landed) {
           ok = false;
           break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int jc = wi; jc < a.bn; jc += kSpEpiPerQuarter) {
-          uint32_t vh, vl;  // W X_hi and W X_lo of this pair
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                       : "=r"(vh)
-                       : "r"(tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols + jc)));
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                       : "=r"(vl)
-                       : "r"(tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols + a.bn + jc)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const float hraw = __fadd_rn(__uint_as_float(vh), __uint_as_float(vl));
-          const unsigned r = static_cast<unsigned>(tn * a.bn + jc);
-          const bool pair_ok = row_ok && r < static_cast<unsigned>(a.R);
-          df mn[3], ms[3], ks[3];
-          if (a.staged) {
-            cp_async_wait_all();
-#pragma unroll
-            for (int qq = 0; qq < 3; ++qq) {
-              const float2 x0 = stg[qq * 32 + lane];
-              mn[qq] = df{x0.x, x0.y};
-              if (st > 0) {
-                const float2 x1 = stg[(3 + qq) * 32 + lane], x2 = stg[(6 + qq) * 32 + lane];
-                ms[qq] = df{x1.x, x1.y};
-                ks[qq] = df{x2.x, x2.y};
-              }
-            }
-            if (jc + kSpEpiPerQuarter < a.bn) prefetch(jc + kSpEpiPerQuarter);
-          } else if (pair_ok) {
-            const size_t idx = static_cast<size_t>(r) * a.N + k;
-#pragma unroll
-            for (int qq = 0; qq < 3; ++qq) {
-              const float2 x0 = a.mn[qq * RN + idx];
-              mn[qq] = df{x0.x, x0.y};
-              if (st > 0) {
-                const float2 x1 = a.ms[qq * RN + idx], x2 = a.ksum[qq * RN + idx];
-                ms[qq] = df{x1.x, x1.y};
-                ks[qq] = df{x2.x, x2.y};
-              }
-            }
-          }
-          if (pair_ok) {
-            const size_t xo = xk + static_cast<size_t>(jc * 64 + ((kchunk ^ (jc & 7u)) << 3));
-            sweep_pair(a, r, k, hraw, st, t, sample, drive, mn, ms, ks, Xn, xo, lo_off);
-          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();

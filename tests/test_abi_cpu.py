@@ -112,3 +112,10 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.sto_run(None, buf, 1, None) == sto.STO_EINVAL
     assert lib.sto_get_info(None, None) == sto.STO_EINVAL
     lib.sto_destroy(None)
+    b = ctypes.c_void_p()
+    assert lib.sto_batch_create(2, 0, ctypes.byref(cp), None, None, buf, buf, None, None,
+                                ctypes.byref(b)) == sto.STO_EINVAL
+    # the sweep's update indexes its [3][R][N] state with 32-bit offsets: R N <= 2^29
+    for N, R in ((32769, 1), (1, 65537), (20000, 30000)):
+        assert lib.sto_batch_create(N, R, ctypes.byref(cp), None, None, buf, buf, None, None,
+                                    ctypes.byref(b)) == sto.STO_ENOTSUP, (N, R)
