@@ -371,11 +371,13 @@ typedef struct {
   int32_t reserved[2];
 } sto_batch_plan;
 
-/* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (3 to 9:
- * three copy warps, warp p owning the slots s = p mod 3; the state staging
- * buffer is used when it fits beside the ring), with one reservoir group, or
- * (0, 0) to time every candidate (tile_n in {16, 32, 40, 48, 64, ..., 128} up
- * to R, slots in {3, 4, 5, 6}, staging on and off, 1 and 2 groups) on two RK4 steps of zero
+/* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (2 to 9 ring
+ * slots of two 64-wide K slices each: 2 (16 KB + 256 tile_n B) of shared
+ * memory per slot; three copy warps, warp p owning the slots s = p mod 3;
+ * the state staging buffer is used when it fits beside the ring), with one
+ * reservoir group, or (0, 0) to time every candidate (tile_n in {16, 32, 40,
+ * 48, 64, ..., 128} up to R, slots in {2, 3, 4, 5}, staging on and off, 1 and
+ * 2 groups) on two RK4 steps of zero
  * input from the batch's state (restored afterwards) and keep the fastest.
  * Tuned plans are cached per (device, N, R) for the life of the process.
  * The stage state is kept.

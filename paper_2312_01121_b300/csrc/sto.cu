@@ -1421,8 +1421,7 @@ void free_batch(sto_batch* b) {
 // memory within the device limit, every CTA resident (one per SM), and with
 // two groups at least two tile columns.
 bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, SweepPlan* out) {
-  if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < sto::kSpProducers || slots > sto::kSpMaxSlots ||
-      groups < 1 || groups > 2)
+  if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < 2 || slots > sto::kSpMaxSlots || groups < 1 || groups > 2)
     return false;
   SweepPlan p;
   p.bn = bn;
@@ -1434,7 +1433,7 @@ bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, S
   p.tn_split = groups == 2 ? (p.tiles_n + 1) / 2 : p.tiles_n;
   p.acc_cols = 2 * bn <= 32 ? 32 : (2 * bn <= 64 ? 64 : (2 * bn <= 128 ? 128 : 256));  // [hi | lo] columns
   p.staged = staged ? 1 : 0;
-  p.smem = static_cast<size_t>(slots) * (sto::kSwSliceA + 2u * bn * sto::kSwK * 2u) +
+  p.smem = static_cast<size_t>(slots) * sto::kSlotK * (sto::kSwSliceA + 2u * bn * sto::kSwK * 2u) +
            (staged ? sto::kSpStageAll : 0) + sto::kSpAlignSlack;
   const int room = raise_dyn_smem_cap(sto::sweep_persistent_kernel);
   if (room < 0 || p.smem > static_cast<size_t>(room)) return false;
@@ -1540,7 +1539,7 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
 
 // Tile widths, ring depths and group counts the autotuner times.
 constexpr int kTuneBn[] = {16, 32, 40, 48, 64, 80, 96, 112, 128};
-constexpr int kTuneSlots[] = {3, 4, 5, 6};
+constexpr int kTuneSlots[] = {2, 3, 4, 5};
 constexpr int kTuneGroups[] = {1, 2};
 
 struct TuneKey {
@@ -1697,7 +1696,8 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
   b->R = R;
   b->params = *params;
   b->Mpad = static_cast<int>((N + sto::kSwM - 1) / sto::kSwM * sto::kSwM);
-  b->Kpad = static_cast<int>((N + sto::kSwK - 1) / sto::kSwK * sto::kSwK);
+  constexpr int kKStep = sto::kSlotK * sto::kSwK;  // whole ring slots of K
+  b->Kpad = static_cast<int>((N + kKStep - 1) / kKStep * kKStep);
   cudaStream_t s = b->stream;
   auto fail = [&](int code) {
     if (b->stream) cudaStreamSynchronize(b->stream);

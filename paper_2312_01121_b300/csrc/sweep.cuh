@@ -14,8 +14,9 @@
 // One persistent cooperative launch runs a whole sto_run_batched call.  The
 // product is cut into tiles of 128 oscillators x BN reservoirs.  Warp 0
 // issues the MMAs of a tile into one of two tensor-memory accumulators while
-// warps 1-3 stream its K slices (one W slice and the matching X_hi and X_lo
-// slices, 1-D bulk copies) through a shared-memory ring; the other 28 warps
+// warps 1-3 stream its K slices (kSlotK W slices and the matching X_hi and
+// X_lo slices per ring slot, two 1-D bulk copies) through a shared-memory
+// ring; the other 28 warps
 // read a finished accumulator with tcgen05.ld and run the per-pair epilogue
 // (double-float torque, RK4 combination, BF16 split of the next X, sampling)
 // while the next tile's MMAs fill the other accumulator.
@@ -57,10 +58,14 @@ namespace sto {
 constexpr int kSwM = 128;          // tile rows (oscillators) = TMEM lanes
 constexpr int kSwK = 64;           // K slice per copy
 constexpr int kSwSliceA = kSwM * kSwK * 2;             // 16 KB of W per slice
+// K slices per ring slot: one wait, 8 MMAs and one commit per slot (the
+// MMA thread's fixed cost per slot is about that of 4 MMAs); Kpad is a
+// multiple of kSlotK * kSwK
+constexpr int kSlotK = 2;
 constexpr int kSpEpiPerQuarter = 7;                    // epilogue warps per TMEM lane quarter
 constexpr int kSpEpiWarps = 4 * kSpEpiPerQuarter;      // 28
 // Three warps issue the copies, warp p owning the ring slots s = p (mod 3);
-// the ring holds 3 to 9 slots.
+// the ring holds 2 to 9 slots (with 2 the third copy warp idles).
 constexpr int kSpProducers = 3;
 constexpr int kSpEpiFirst = 1 + kSpProducers;          // warp 0 multiplies, 1..3 copy
 constexpr int kSpThreads = 32 * (kSpEpiFirst + kSpEpiWarps);  // 1024
@@ -254,10 +259,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int q, int idx, i
   *tn = idx / a.tiles_m + (q == 0 ? 0 : a.tn_split);
 }
 
-// The whole sweep call: 4 S T stages of every group.  Warp 0 (one thread)
-// passes each unit's group barrier, releases the unit to the copy warps and
-// issues the MMAs; warps 1-3 (one thread each) fill their ring slots; warps
-// 4-31 run the epilogue.
 // The epilogue of one tile for one epilogue warp: the pairs (reservoir
 // tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + 7, ...
 // The state of the next column's pair is copied into shared memory (stg)
@@ -335,6 +336,10 @@ __device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, float2* st
   return true;
 }
 
+// The whole sweep call: 4 S T stages of every group.  Warp 0 (one thread)
+// passes each unit's group barrier, releases the unit to the copy warps and
+// issues the MMAs; warps 1-3 (one thread each) fill their ring slots; warps
+// 4-31 run the epilogue.
 __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
   // the swizzle pattern repeats every 1024 B: the ring starts on such a boundary
@@ -354,7 +359,9 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
   auto n_my = [&](int q) { return q == 0 ? my0 : my1; };
   const int nk = a.Kpad / kSwK;
   const uint32_t sliceB = static_cast<uint32_t>(a.bn) * kSwK * 2;  // one X slice (hi or lo)
-  const uint32_t slot_bytes = kSwSliceA + 2 * sliceB;
+  // slot: kSlotK W slices, then the kSlotK matching [X_hi | X_lo] slices
+  const uint32_t slot_bytes = kSlotK * (kSwSliceA + 2 * sliceB);
+  const int nkk = nk / kSlotK;  // slots per tile
   const long long n_stages = 4LL * a.S * a.T;
   const long long n_units = n_stages * n_grp;
   const volatile int* abort_flag = &s_abort;
@@ -396,6 +403,12 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
       // division by the ring depth per K slice cost more than its MMAs)
       int s = 0;
       uint32_t ph = 0;
+      // shared-memory descriptors of the slot's operands (umma_desc_sw128) as
+      // two 32-bit words: the start address advances by 32 B (2 in the
+      // address field) per K step of 16; the high word is the same for all
+      const uint32_t slot0 = smem_u32(sp_smem);
+      const uint32_t d_hi = static_cast<uint32_t>(umma_desc_sw128(slot0) >> 32);
+      uint32_t a_addr = slot0;  // slot s
       bool ok = true;
       for (long long u = 0; u < n_units && ok; ++u) {
         const long long g = u / n_grp;
@@ -426,7 +439,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         st_release_cta_u64(&s_go, static_cast<unsigned long long>(u + 1));  // the copy warps may read this unit's X
         for (int i = 0; i < nm && ok; ++i) {
           const long long sq = seq + i;
-          for (int j = 0; j < nk; ++j) {
+          for (int j = 0; j < nkk; ++j) {
             const int b = static_cast<int>(sq & 1);
             if (j == 0 && sq >= 2) {
               // the epilogue has read this accumulator's previous tile
@@ -441,26 +454,33 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sp_smem + static_cast<size_t>(s) * slot_bytes);
-            const uint32_t b0 = a0 + kSwSliceA;
             const uint32_t dt = tmem + static_cast<uint32_t>(b * a.acc_cols);
 #pragma unroll
-            for (int jk = 0; jk < kSwK / 16; ++jk) {
-              // B: the X_hi slice and the X_lo slice behind it, 2 bn rows
-              const uint64_t ad = umma_desc_sw128(a0 + jk * 32);
-              const uint64_t bd = umma_desc_sw128(b0 + jk * 32);
-              const uint32_t accum = (j > 0 || jk > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                  : "memory");
+            for (int h = 0; h < kSlotK; ++h) {
+              const uint32_t a_lo = static_cast<uint32_t>(umma_desc_sw128(a_addr + h * kSwSliceA));
+              const uint32_t b_lo =
+                  static_cast<uint32_t>(umma_desc_sw128(a_addr + kSlotK * kSwSliceA + h * 2 * sliceB));
+#pragma unroll
+              for (int jk = 0; jk < kSwK / 16; ++jk) {
+                // B: the X_hi slice and the X_lo slice behind it, 2 bn rows
+                const uint32_t accum = (j > 0 || h > 0 || jk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\t"
+                    "setp.ne.u32 p, %4, 0;\n\t"
+                    "mov.b64 ad, {%1, %5};\n\t"
+                    "mov.b64 bd, {%2, %5};\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %3, p;\n\t}" ::"r"(dt),
+                    "r"(a_lo + 2u * jk), "r"(b_lo + 2u * jk), "r"(idesc), "r"(accum), "r"(d_hi)
+                    : "memory");
+              }
             }
             umma_commit(&empty[s]);
-            if (j == nk - 1) umma_commit(&acc_full[b]);
+            if (j == nkk - 1) umma_commit(&acc_full[b]);
+            a_addr += slot_bytes;
             if (++s == a.slots) {
               s = 0;
               ph ^= 1u;
+              a_addr = slot0;
             }
           }
         }
@@ -509,7 +529,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
           sweep_tile(a, q, cta + i * G, &tm, &tn);
           const __nv_bfloat16* Wt = a.Wb + static_cast<size_t>(tm) * nk * (kSwM * kSwK);
           const __nv_bfloat16* xt = X + static_cast<size_t>(tn) * nk * (2 * a.bn * kSwK);
-          for (int j = 0; j < nk; ++j, ++P) {
+          for (int j = 0; j < nkk; ++j, ++P) {
             if (s % kSpProducers == pid) {
               // the slot's previous use (lap - 1, parity ph ^ 1) has been consumed
               if (P >= a.slots && !mbar_wait_bounded(&empty[s], ph ^ 1u, a.timeout_ns, abort_flag)) {
@@ -518,9 +538,11 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
               }
               unsigned char* slot = sp_smem + static_cast<size_t>(s) * slot_bytes;
               mbar_arrive_expect_tx(&full[s], slot_bytes);
-              bulk_g2s(slot, Wt + static_cast<size_t>(j) * (kSwM * kSwK), kSwSliceA, &full[s], pol);
-              bulk_g2s(slot + kSwSliceA, xt + static_cast<size_t>(j) * (2 * a.bn * kSwK), 2 * sliceB, &full[s],
-                       pol);  // X_hi and X_lo rows
+              // K slices kSlotK j .. kSlotK j + kSlotK - 1 are adjacent tiles of both operands
+              bulk_g2s(slot, Wt + static_cast<size_t>(kSlotK * j) * (kSwM * kSwK), kSlotK * kSwSliceA, &full[s],
+                       pol);
+              bulk_g2s(slot + kSlotK * kSwSliceA, xt + static_cast<size_t>(kSlotK * j) * (2 * a.bn * kSwK),
+                       kSlotK * 2 * sliceB, &full[s], pol);  // X_hi and X_lo rows
               last = P;
             }
             if (++s == a.slots) {

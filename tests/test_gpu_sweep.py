@@ -117,9 +117,9 @@ def test_group_of_own_w_reservoirs_matches_separate_runs(sto):
     assert np.max(np.abs(outs[0] - orc)) <= 1e-5
 
 
-@pytest.mark.parametrize("tile_n,slots,groups", [(16, 3, 1), (32, 6, 1), (48, 3, 1), (80, 3, 1), (80, 4, 1),
-                                                 (64, 5, 1), (80, 6, 1), (112, 3, 1), (128, 3, 1), (16, 6, 2),
-                                                 (24, 3, 2), (40, 3, 2), (48, 3, 2), (32, 7, 2)])
+@pytest.mark.parametrize("tile_n,slots,groups", [(16, 3, 1), (32, 4, 1), (48, 3, 1), (80, 2, 1), (80, 3, 1),
+                                                 (64, 3, 1), (16, 5, 1), (112, 2, 1), (128, 2, 1), (16, 4, 2),
+                                                 (24, 3, 2), (40, 2, 2), (48, 3, 2), (32, 4, 2)])
 def test_sweep_forced_plans_match_oracle(sto, tile_n, slots, groups):
     """Every tile width, ring depth (also depths that are not a multiple of
     the three copy warps, which then own unequal numbers of slots) and group
@@ -183,7 +183,9 @@ def test_sweep_autotuner_and_invalid_plans(sto):
         with pytest.raises(sto.StoError):
             sw.set_plan(64, 3, 3)  # at most two reservoir groups
         with pytest.raises(sto.StoError):
-            sw.set_plan(64, 9)  # ring deeper than the kernel allows
+            sw.set_plan(64, 9)  # ring deeper than shared memory allows
+        with pytest.raises(sto.StoError):
+            sw.set_plan(64, 1)  # at least two ring slots
         st = np.zeros((T, R, N), np.float32)
         sw.run(u, st)
         plan = sw.plan()
@@ -199,7 +201,7 @@ def test_sweep_autotuner_and_invalid_plans(sto):
 
 
 @pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3),
-                                              (1000, 65, 32, 6), (2500, 512, 40, 5)])
+                                              (1000, 65, 32, 4), (2500, 512, 40, 2)])
 def test_sweep_two_groups_bitwise_equal_to_one(sto, N, R, tile_n, slots):
     """Two reservoir groups with their own barriers only reorder independent
     work: every tile's product and every pair's update are the same
