@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--sweep-n", type=int, default=2500)
     ap.add_argument("--sweep-r", type=int, default=512)
     ap.add_argument("--sweep-t", type=int, default=2, help="input samples per timed sweep call")
-    ap.add_argument("--sweep-plan", default="", help="tile_n,slots of the sweep kernel (default: autotuned)")
+    ap.add_argument("--sweep-plan", default="",
+                    help="tile_n,slots[,groups[,staged]] of the sweep kernel (default: autotuned)")
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
@@ -355,7 +356,7 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
     sw.close()
     stages = 4 * args.substeps * T
     us_stage = ms * 1e3 / stages
-    Mpad, Kpad = -(-N // 128) * 128, -(-N // 64) * 64
+    Mpad, Kpad = -(-N // 128) * 128, -(-N // 128) * 128  # K is padded to whole ring slots of 2 x 64
     Rpad = -(-R // plan["tile_n"]) * plan["tile_n"]
     alg_flop = 2.0 * N * N * R            # the coupling product W X of one stage
     exe_flop = 2.0 * Mpad * (2 * Kpad) * Rpad  # executed: hi/lo split, padded tiles

@@ -393,6 +393,15 @@ STO_API int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots);
  * STO_EINVAL for groups outside 1..2. */
 STO_API int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups);
 
+/* sto_batch_set_plan_ex with the staging mode: staged = 1 copies each
+ * pair's state into shared memory ahead of its update (STO_ENOTSUP when it
+ * does not fit beside the ring), 0 reads it from global memory in the
+ * update, -1 stages when it fits (as sto_batch_set_plan_ex).  Lets a caller
+ * (or a profiler run) fix exactly the plan the autotuner chose.  Errors: as
+ * sto_batch_set_plan_ex; STO_EINVAL for staged outside -1..1. */
+STO_API int sto_batch_set_plan_staged(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups,
+                                      int32_t staged);
+
 /* The current plan (all zero before the first run or set_plan). */
 STO_API int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out);
 

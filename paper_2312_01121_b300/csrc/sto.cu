@@ -1807,14 +1807,20 @@ int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots) {
 }
 
 int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups) {
+  return sto_batch_set_plan_staged(b, tile_n, slots, groups, -1);
+}
+
+int sto_batch_set_plan_staged(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups, int32_t staged) {
   if (!b) return STO_EINVAL;
-  if (groups < 1 || groups > 2) return STO_EINVAL;
+  if (groups < 1 || groups > 2 || staged < -1 || staged > 1) return STO_EINVAL;
   cudaStreamSynchronize(b->stream);
   if (tile_n == 0 && slots == 0) return sweep_autotune(b);
   SweepPlan p;
-  // stage the epilogue's state through shared memory when it fits beside the ring
-  if (!sweep_plan(b, tile_n, slots, 1, groups, &p) && !sweep_plan(b, tile_n, slots, 0, groups, &p))
-    return STO_ENOTSUP;
+  // staged = -1: stage the epilogue's state through shared memory when it fits beside the ring
+  const bool found = staged == -1 ? (sweep_plan(b, tile_n, slots, 1, groups, &p) ||
+                                     sweep_plan(b, tile_n, slots, 0, groups, &p))
+                                  : sweep_plan(b, tile_n, slots, staged, groups, &p);
+  if (!found) return STO_ENOTSUP;
   int rc = sweep_apply_plan(b, p);
   if (rc) return rc;
   b->tuned = 0;

@@ -108,6 +108,7 @@ SIGNATURES = {
     "sto_batch_destroy": (None, [_VP]),
     "sto_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32]),
     "sto_batch_set_plan_ex": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
+    "sto_batch_set_plan_staged": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "sto_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(sto_batch_plan)]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
@@ -542,10 +543,11 @@ class Sweep:
         _check(load_library().sto_batch_get_state(self.handle, out.ctypes.data))
         return out
 
-    def set_plan(self, tile_n: int = 0, slots: int = 0, groups: int = 1):
-        """Force a tile width / ring depth / reservoir-group count, or (0, 0)
-        to run the autotuner."""
-        _check(load_library().sto_batch_set_plan_ex(self.handle, int(tile_n), int(slots), int(groups)))
+    def set_plan(self, tile_n: int = 0, slots: int = 0, groups: int = 1, staged: int = -1):
+        """Force a tile width / ring depth / reservoir-group count and staging
+        mode (1, 0, or -1 = when it fits), or (0, 0) to run the autotuner."""
+        _check(load_library().sto_batch_set_plan_staged(self.handle, int(tile_n), int(slots), int(groups),
+                                                        int(staged)))
 
     def plan(self) -> dict:
         p = sto_batch_plan()

@@ -195,9 +195,17 @@ def test_sweep_autotuner_and_invalid_plans(sto):
         # the tuner restored the state it ran from: same samples as a forced plan
         ref = np.zeros_like(st)
         with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw2:
-            sw2.set_plan(plan["tile_n"], plan["slots"], plan["groups"])
+            sw2.set_plan(plan["tile_n"], plan["slots"], plan["groups"], plan["staged"])
             sw2.run(u, ref)
         assert np.array_equal(st, ref)
+    with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw:
+        with pytest.raises(sto.StoError):
+            sw.set_plan(128, 2, 1, 1)  # staging does not fit beside two 96 KB slots
+        with pytest.raises(sto.StoError):
+            sw.set_plan(64, 3, 1, 2)  # staging mode outside -1..1
+        for staged in (0, 1):
+            sw.set_plan(40, 2, 1, staged)
+            assert sw.plan()["staged"] == staged
 
 
 @pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3),
