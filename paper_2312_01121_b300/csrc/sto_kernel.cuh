@@ -576,6 +576,7 @@ struct AdjointProgram {
   float hraw[4];
   df gacp, gcur, sumg, hin;
   long long n;        // current RK4 step (counting down)
+  int nt, nsb;        // n = nt S + nsb: its input sample and substep (counted, not divided)
   int si;             // current stage index 0..3 (stage 1..4)
 
   __device__ __forceinline__ static void cross(const df a[3], const df b[3], df r[3]) {
@@ -589,7 +590,7 @@ struct AdjointProgram {
 
   __device__ __forceinline__ void setup_step(const KArgs& a, int node) {
     const int S = a.S;
-    const int t = static_cast<int>(n / S), sb = static_cast<int>(n % S);
+    const int t = nt, sb = nsb;
     if (sb == S - 1) {  // the state after this step is sample t; its input field
       lam[a.comp] = df_add_f(lam[a.comp], a.dLds[static_cast<size_t>(t) * a.N + node]);
       double s = 0.0;
@@ -699,6 +700,8 @@ struct AdjointProgram {
     for (int i = 0; i < 3; ++i) lam[i] = df_from_double(a.lam[static_cast<size_t>(i) * a.N + node]);
     gacp = gcur = sumg = hin = df{0.f, 0.f};
     n = static_cast<long long>(a.T) * a.S - 1;
+    nt = a.T - 1;
+    nsb = a.S - 1;
     setup_step(a, node);
     si = 3;
     const df zero[3] = {df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}};
@@ -723,8 +726,8 @@ struct AdjointProgram {
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) lam[i] = df_add(lam[i], lacc[i]);
-    if (n % a.S == 0) {  // first RK4 step of its sample: flush dL/dw_in
-      const int t = static_cast<int>(n / a.S);
+    if (nsb == 0) {  // first RK4 step of its sample: flush dL/dw_in
+      const int t = nt;
       const double sg = df_to_double(sumg);
       for (int jj = 0; jj < a.n_in; ++jj)
         a.g_win[static_cast<size_t>(node) * a.n_in + jj] +=
@@ -732,6 +735,12 @@ struct AdjointProgram {
       sumg = df{0.f, 0.f};
     }
     if (--n >= 0) {
+      if (nsb == 0) {
+        nsb = a.S - 1;
+        --nt;
+      } else {
+        --nsb;
+      }
       setup_step(a, node);
       si = 3;
       const df zero[3] = {df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}};
