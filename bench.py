@@ -369,6 +369,12 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
             "tensor_peak_tflops": peaks.get("bf16"),
             "frac_of_bf16_peak_whole_stage": (exe_flop / (us_stage * 1e-6) / 1e12) / peaks["bf16"]
             if peaks.get("bf16") else None,
+            # the per-pair RK4 state (mn, ms, ksum as double-float triples) is read and written
+            # every stage: on average 60 B read + 42 B written per pair and stage (stage 0 reads
+            # mn only, stage 3 writes mn only), the other roofline of this kernel
+            "state_bytes_per_stage": 102.0 * R * N,
+            "state_gbs": 102.0 * R * N / (us_stage * 1e-6) / 1e9,
+            "frac_of_hbm_state": (102.0 * R * N / (us_stage * 1e-6) / 1e9) / measured_peaks()[0],
             "finite": finite, "plan": plan,
             "launches_per_call": 1}
 
