@@ -216,6 +216,9 @@ cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStr
 
 cudaError_t launch_adjoint(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   constexpr int A = sto::kProgAdjoint;
+  // W^T is tiled like W, so a register-resident plan holds W^T the same way
+  if (pl.regw) return pl.rpw <= 1 ? launch_rpw<1, false, A, sto::kWf32, true>(pl, a, s)
+                                  : launch_rpw<2, false, A, sto::kWf32, true>(pl, a, s);
   if (pl.rpw <= 1) return launch_rpw<1, false, A>(pl, a, s);
   if (pl.rpw <= 2) return launch_rpw<2, false, A>(pl, a, s);
   if (pl.rpw <= 4) return launch_rpw<4, false, A>(pl, a, s);
