@@ -114,7 +114,12 @@ struct sto_handle {
   float* d_W = nullptr;
   float* d_win = nullptr;
   double* d_state = nullptr;
-  unsigned long long* d_xbuf = nullptr;
+  unsigned long long* d_xbuf = nullptr;       // the exchange buffer in use, inside the pool
+  unsigned long long* d_xbuf_pool = nullptr;  // xbuf_n candidate placements, xbuf_stride bytes apart
+  int xbuf_n = 1;
+  size_t xbuf_stride = 0;
+  int xbuf_slot = 0;
+  int xbuf_timed = 0;  // placements timed at creation (0: not tuned)
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned, 4 ints
   float* d_u = nullptr;
@@ -140,7 +145,7 @@ void free_handle(sto_handle* h) {
   cudaFree(h->d_W);
   cudaFree(h->d_win);
   cudaFree(h->d_state);
-  cudaFree(h->d_xbuf);
+  cudaFree(h->d_xbuf_pool);
   cudaFree(h->d_err);
   cudaFree(h->d_u);
   cudaFree(h->d_states);
@@ -392,6 +397,11 @@ size_t xbuf_bytes(int64_t N, int wmode) {
   return 2 * static_cast<size_t>(N) * 8 * (wmode == sto::kWf32 ? 1 : 2);
 }
 
+// Candidate placements of the exchange buffer for plans with W on chip (see
+// tune_xbuf), each on its own 4 KB-aligned block.
+constexpr int kXbufCandidates = 8;
+size_t xbuf_stride_bytes(int64_t N, int wmode) { return (xbuf_bytes(N, wmode) + 4095) / 4096 * 4096; }
+
 // Kernel arguments shared by the forward and adjoint launches of a handle.
 sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   const sto_params& P = h->params;
@@ -426,7 +436,7 @@ sto::KArgs base_args(sto_handle* h, const float* d_u, int64_t T) {
   const uint64_t stages = static_cast<uint64_t>(h->rk_stages) * static_cast<uint64_t>(P.substeps) *
                           static_cast<uint64_t>(T);
   if (h->stage_counter + stages + 2 >= 0xfffffff0ULL) {
-    cudaMemsetAsync(h->d_xbuf, 0xff, xbuf_bytes(h->N, h->wmode), h->stream);
+    cudaMemsetAsync(h->d_xbuf_pool, 0xff, h->xbuf_n * h->xbuf_stride, h->stream);
     h->stage_counter = 0;
   }
   const uint64_t base = h->stage_counter + 1;
@@ -482,6 +492,83 @@ int finish_launch(sto_handle* h) {
   h->inject_cta = -1;
   if (h->h_err[0] != 0) return h->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
   return STO_OK;
+}
+
+// Placement of the exchange buffer.  With W on chip a stage is one exchange
+// round trip: every CTA polls the lines of the tagged words, one line per
+// owning CTA, and how those lines fall on the L2 slices sets how long the
+// slowest poll takes (measured at N = 10^3 on one device: 1.62-1.72 us per
+// stage for some buffers, 1.9-2.4 us for others, the same plan and data).
+// Time a short launch (zero input, at most 50 RK4 steps) in each candidate
+// block of the pool, the best of three, keep the fastest, and restore the
+// state.  Placement changes no arithmetic: the results are the same bits.
+int tune_xbuf(sto_handle* h) {
+  if (h->xbuf_n <= 1) return STO_OK;
+  const size_t sbytes = 3 * static_cast<size_t>(h->N) * sizeof(double);
+  double* saved = nullptr;
+  float* u0 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(saved);
+    cudaFree(u0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(reinterpret_cast<void**>(&saved), sbytes) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&u0), static_cast<size_t>(h->params.n_in) * sizeof(float)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return STO_ENOMEM;
+  }
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+      (e = cudaMemsetAsync(u0, 0, static_cast<size_t>(h->params.n_in) * sizeof(float), h->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(saved, h->d_state, sbytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e);
+  }
+  const int substeps = h->params.substeps;
+  h->params.substeps = substeps < 50 ? substeps : 50;
+  int rc = STO_OK, best = 0;
+  float best_ms = 0.f;
+  for (int c = 0; c < h->xbuf_n && rc == STO_OK; ++c) {
+    h->d_xbuf = h->d_xbuf_pool + c * (h->xbuf_stride / sizeof(unsigned long long));
+    float ms_c = 0.f;
+    for (int rep = 0; rep < 3 && rc == STO_OK; ++rep) {
+      if ((e = cudaEventRecord(e0, h->stream)) != cudaSuccess) {
+        rc = cuda_fail(e);
+        break;
+      }
+      rc = engine_launch(h, u0, 1, nullptr, nullptr, nullptr);
+      if (rc) break;
+      if ((e = cudaEventRecord(e1, h->stream)) != cudaSuccess) {
+        rc = cuda_fail(e);
+        break;
+      }
+      rc = finish_launch(h);
+      float ms = 0.f;
+      if (!rc && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) rc = cuda_fail(e);
+      if (!rc && (rep == 0 || ms < ms_c)) ms_c = ms;
+    }
+    if (!rc && (c == 0 || ms_c < best_ms)) {
+      best_ms = ms_c;
+      best = c;
+    }
+  }
+  h->params.substeps = substeps;
+  h->d_xbuf = h->d_xbuf_pool + best * (h->xbuf_stride / sizeof(unsigned long long));
+  if (rc == STO_OK) {
+    h->xbuf_slot = best;
+    h->xbuf_timed = h->xbuf_n;
+  }
+  // back to the state before the trial launches
+  if ((e = cudaMemcpyAsync(h->d_state, saved, sbytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    if (rc == STO_OK) rc = cuda_fail(e);
+  cleanup();
+  return rc;
 }
 
 // W^T in the tiled layout of the plan, derived from the tiled W.
@@ -546,6 +633,8 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
 
   const int n_in = params->n_in;
   const size_t wt_elems = static_cast<size_t>(N) * h->plan.P * sto::kPanelCols;
+  h->xbuf_n = (h->plan.resident && h->plan.G > 1) ? kXbufCandidates : 1;
+  h->xbuf_stride = xbuf_stride_bytes(N, wmode);
   auto alloc = [&](void** p, size_t bytes) -> bool {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -557,7 +646,7 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
   if (!alloc(reinterpret_cast<void**>(&h->d_W), wt_elems * 4) ||
       !alloc(reinterpret_cast<void**>(&h->d_win), static_cast<size_t>(N) * n_in * 4) ||
       !alloc(reinterpret_cast<void**>(&h->d_state), 3 * static_cast<size_t>(N) * 8) ||
-      !alloc(reinterpret_cast<void**>(&h->d_xbuf), xbuf_bytes(N, wmode)) ||
+      !alloc(reinterpret_cast<void**>(&h->d_xbuf_pool), h->xbuf_n * h->xbuf_stride) ||
       !alloc(reinterpret_cast<void**>(&h->d_err), 16))
     return fail(STO_ENOMEM);
   if (cudaMallocHost(reinterpret_cast<void**>(&h->h_err), 16) != cudaSuccess) {
@@ -611,7 +700,8 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
   if (rc) return fail(rc);
 
   // exchange buffer: tag 0xffffffff is never used by a launch
-  e = cudaMemsetAsync(h->d_xbuf, 0xff, xbuf_bytes(N, wmode), s);
+  h->d_xbuf = h->d_xbuf_pool;
+  e = cudaMemsetAsync(h->d_xbuf_pool, 0xff, h->xbuf_n * h->xbuf_stride, s);
   if (e != cudaSuccess) return fail(cuda_fail(e));
 
   // state
@@ -634,6 +724,7 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
     }
   }
   rc = set_state_host_f64(h, m.data());
+  if (!rc) rc = tune_xbuf(h);
   if (rc) return fail(rc);
   *out = h;
   return STO_OK;
@@ -786,6 +877,8 @@ int sto_get_info(const sto_handle* h, sto_info* out) {
   out->smem_bytes = static_cast<int32_t>(h->plan.smem);
   out->sm_count = h->sm_count;
   out->w_bytes = w_elem_bytes(h->wmode) * h->N * h->N;
+  out->xbuf_timed = h->xbuf_timed;
+  out->xbuf_slot = h->xbuf_slot;
   return STO_OK;
 }
 

@@ -65,7 +65,7 @@ class sto_info(ctypes.Structure):
                 ("panel_cols", ctypes.c_int32), ("panels", ctypes.c_int32),
                 ("ring_slots", ctypes.c_int32), ("resident", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("sm_count", ctypes.c_int32),
-                ("w_bytes", ctypes.c_int64)]
+                ("w_bytes", ctypes.c_int64), ("xbuf_timed", ctypes.c_int32), ("xbuf_slot", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
