@@ -73,7 +73,7 @@ extern "C" {
 #define STO_ECUDA (-3)       /* a CUDA runtime call failed (see sto_strerror) */
 #define STO_ETIMEOUT (-4)    /* a device-side wait exceeded its time limit */
 #define STO_ENONFINITE (-5)  /* NaN or Inf found in an input */
-#define STO_ENOTSUP (-6)     /* size or option outside what this build supports */
+#define STO_ENOTSUP (-6)     /* size or option outside what the library supports */
 #define STO_ETOOBIG (-7)     /* N above the static scratch of sto_run_noalloc */
 
 /* Model parameters.  Defaults (sto_default_params) are Table "Summary of

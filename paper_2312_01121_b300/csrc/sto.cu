@@ -818,7 +818,7 @@ const char* sto_strerror(int code) {
     case STO_ECUDA: base = "CUDA error"; break;
     case STO_ETIMEOUT: base = "device wait timed out"; break;
     case STO_ENONFINITE: base = "non-finite input"; break;
-    case STO_ENOTSUP: base = "not supported by this build"; break;
+    case STO_ENOTSUP: base = "size or option not supported by the library"; break;
     case STO_ETOOBIG: base = "size exceeds the static scratch of sto_run_noalloc (N <= 16384)"; break;
     default: break;
   }
