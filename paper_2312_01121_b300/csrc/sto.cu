@@ -1206,6 +1206,11 @@ int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group*
     load[best] += cost[i];
     lane_jobs[best].push_back(i);
   }
+  // odd lanes run their jobs shortest first, so that while some lanes
+  // stream large W from HBM the others run small, latency-bound members
+  // (largest first everywhere puts every lane on HBM at the start and every
+  // lane on latency-bound members at the end)
+  for (int l = 1; l < L; l += 2) std::reverse(lane_jobs[l].begin(), lane_jobs[l].end());
   g->lane_begin.push_back(0);
   for (int l = 0; l < L; ++l) {
     for (int j : lane_jobs[l]) g->order.push_back(j);
