@@ -125,10 +125,11 @@ typedef struct sto_info {
   int32_t sm_count;      /* SMs of the device */
   int64_t w_bytes;       /* bytes of W streamed per RK4 stage (4 N^2, or
                             8 N^2 for sto_create_f64) */
-  int32_t xbuf_timed;    /* placements of the exchange buffer timed at
-                            creation (8 when W is on chip and G > 1: the
-                            stage time depends on where the polled lines
-                            fall in the L2; 0 otherwise) */
+  int32_t xbuf_timed;    /* placements of the exchange buffer timed at the
+                            handle's first sto_run or sto_adjoint (8 when W
+                            is on chip and G > 1: the stage time depends on
+                            where the polled lines fall in the L2; 0 before
+                            that or otherwise) */
   int32_t xbuf_slot;     /* the placement kept (the fastest) */
 } sto_info;
 

@@ -119,7 +119,8 @@ struct sto_handle {
   int xbuf_n = 1;
   size_t xbuf_stride = 0;
   int xbuf_slot = 0;
-  int xbuf_timed = 0;  // placements timed at creation (0: not tuned)
+  int xbuf_timed = 0;         // placements timed (0: not tuned)
+  bool xbuf_pending = false;  // placements still to time, at the first run or adjoint
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned, 4 ints
   float* d_u = nullptr;
@@ -499,11 +500,14 @@ int finish_launch(sto_handle* h) {
 // owning CTA, and how those lines fall on the L2 slices sets how long the
 // slowest poll takes (measured at N = 10^3 on one device: 1.62-1.72 us per
 // stage for some buffers, 1.9-2.4 us for others, the same plan and data).
-// Time a short launch (zero input, at most 50 RK4 steps) in each candidate
-// block of the pool, the best of three, keep the fastest, and restore the
-// state.  Placement changes no arithmetic: the results are the same bits.
+// At the handle's first sto_run or sto_adjoint (a member run only through a
+// group never pays for it), time a short launch (zero input, at most 50 RK4
+// steps) in each candidate block of the pool, the best of three, keep the
+// fastest, and restore the state.  Placement changes no arithmetic: the
+// results are the same bits.
 int tune_xbuf(sto_handle* h) {
-  if (h->xbuf_n <= 1) return STO_OK;
+  if (!h->xbuf_pending) return STO_OK;
+  h->xbuf_pending = false;
   const size_t sbytes = 3 * static_cast<size_t>(h->N) * sizeof(double);
   double* saved = nullptr;
   float* u0 = nullptr;
@@ -724,8 +728,8 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
     }
   }
   rc = set_state_host_f64(h, m.data());
-  if (!rc) rc = tune_xbuf(h);
   if (rc) return fail(rc);
+  h->xbuf_pending = h->xbuf_n > 1;
   *out = h;
   return STO_OK;
 }
@@ -941,6 +945,7 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
   const size_t n_u = static_cast<size_t>(T) * P.n_in;
   const size_t n_states = static_cast<size_t>(T) * N;
 
+  if (const int rc = tune_xbuf(h)) return rc;
   const float* d_u = u;
   if (!is_device_ptr(u)) {
     int rc = grow(&h->d_u, &h->d_u_cap, n_u);
@@ -973,6 +978,7 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
   const int64_t N = h->N;
   const int n_in = P.n_in;
   cudaStream_t s = h->stream;
+  if (const int rc = tune_xbuf(h)) return rc;
   const int64_t K = ckpt_every < T ? ckpt_every : T;
   const int64_t nseg = (T + K - 1) / K;
   const size_t n3 = 3 * static_cast<size_t>(N);
