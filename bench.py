@@ -241,12 +241,12 @@ def time_device(N, args, ips, seed, torch, sto, dev):
                         l2_keep_mb=args.l2_keep_mb)
     del Wd
     torch.cuda.empty_cache()
-    info = res.info()
     u_d = torch.from_numpy(u).to(dev)
     st_d = torch.empty((ips, N), dtype=torch.float32, device=dev)
-    for i in range(Wm):
+    for i in range(Wm):  # the first run also times the exchange-buffer placements (on-chip W)
         res.run(u_d[i * ips:(i + 1) * ips], st_d)
     torch.cuda.synchronize()
+    info = res.info()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     rank, world, _ = dist_env()
     if world > 1:
