@@ -535,6 +535,8 @@ int tune_xbuf(sto_handle* h) {
   }
   const int substeps = h->params.substeps;
   h->params.substeps = substeps < 50 ? substeps : 50;
+  const int inject = h->inject_cta;  // a stall injected for the next run is kept for that run
+  h->inject_cta = -1;
   int rc = STO_OK, best = 0;
   float best_ms = 0.f;
   for (int c = 0; c < h->xbuf_n && rc == STO_OK; ++c) {
@@ -562,6 +564,7 @@ int tune_xbuf(sto_handle* h) {
     }
   }
   h->params.substeps = substeps;
+  h->inject_cta = inject;
   h->d_xbuf = h->d_xbuf_pool + best * (h->xbuf_stride / sizeof(unsigned long long));
   if (rc == STO_OK) {
     h->xbuf_slot = best;
