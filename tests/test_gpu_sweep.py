@@ -54,6 +54,14 @@ def test_sweep_ragged_tiles(sto):
     _sweep_vs_oracle(sto, N=1000, R=65, T=1, S=3, A_cp=100.0, tol=1e-5, seed=4)
 
 
+@pytest.mark.parametrize("N,R", [(1, 3), (8, 5), (64, 9), (129, 17), (256, 40)])
+def test_sweep_small_and_k_padded_sizes(sto, N, R):
+    """N below one 128-row tile and around the 128-wide K padding of a ring
+    slot (two 64-wide K slices): one slot per tile for N <= 128, two for
+    129 <= N <= 256; N = 1 has W = [0] (Sec. 3.1: no self-coupling)."""
+    _sweep_vs_oracle(sto, N=N, R=R, T=2, S=4, A_cp=60.0, tol=1e-5, seed=30 + N)
+
+
 def test_sweep_first_200_input_samples(sto):
     """The paper's A_in = 1 Oe: outside the chaotic regime (with A_in = 30 Oe
     the FP64 oracle perturbed by 1e-7 in W itself drifts by 1e-4..5e-2 within
