@@ -58,7 +58,7 @@
 extern "C" {
 #endif
 
-#define STO_ABI_VERSION 2
+#define STO_ABI_VERSION 3
 
 #if defined(__GNUC__)
 #define STO_API __attribute__((visibility("default")))
@@ -75,6 +75,7 @@ extern "C" {
 #define STO_ENONFINITE (-5)  /* NaN or Inf found in an input */
 #define STO_ENOTSUP (-6)     /* size or option outside what the library supports */
 #define STO_ETOOBIG (-7)     /* N above the static scratch of sto_run_noalloc */
+#define STO_ESINGULAR (-8)   /* the ridge system of the readout is not positive definite */
 
 /* Model parameters.  Defaults (sto_default_params) are Table "Summary of
  * parameters" of Sec. 3.1 and the step of Sec. 3.2; substeps, n_in,
@@ -463,14 +464,61 @@ STO_API int sto_debug_inject_stall(sto_handle* h, int32_t cta);
  * Every call reuses the same array, which keeps the previous call's
  * contents; the call clears what must start fresh.  Calls that overlap on
  * the GPU (two streams, two threads) race on the array and must be
- * serialised by the caller.  The call synchronises `stream` to read the
- * device error word.
+ * serialised by the caller.  Every call first scans all of W and w_in for
+ * NaN and Inf (4 N^2 + 4 N n_in bytes read, about 0.2 ms at N = 16384) and
+ * synchronises `stream` to read that flag, and synchronises it again at
+ * the end to read the device error word.  The library cannot see the
+ * extents of the caller's arrays: they must hold the sizes above (the
+ * Python binding checks them).
  * Errors: STO_EINVAL (pointer not device memory, N not a multiple of 4,
  *         misaligned W), STO_ETOOBIG, STO_ENONFINITE (W or w_in), STO_ETIMEOUT,
  *         STO_ECUDA, STO_ENOTSUP. */
 STO_API int sto_run_noalloc(int64_t N, const sto_params* params, const float* W,
                             const float* w_in, double* state, const float* u,
                             int64_t T, float* states_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Linear readout of the sampled states.  Sec. 1: in reservoir computing
+ * only the readout is trained; the paper does not specify it further.  The
+ * readout here is linear with a bias, fitted by ridge regression:
+ *     Phi_t = [states[t*N + 0 .. N-1], 1]          (row of N + 1 features)
+ *     w     = argmin sum_t (Phi_t w - y_t)^2 + beta |w_0 .. w_{N-1}|^2
+ *     beta  = beta_rel * trace(Phi^T Phi) / (N + 1) (the bias is not penalised)
+ * solved from the normal equations (Phi^T Phi + beta D) w = Phi^T y by a
+ * Cholesky factorisation, all on the GPU in FP64 (the states are FP32 and
+ * enter exactly).  Each call allocates its scratch (the (N + 2)^2 FP64 Gram
+ * matrix, device copies of host inputs) and frees it before returning, and
+ * synchronises `stream` (cudaStream_t, NULL = legacy default) once.
+ * ------------------------------------------------------------------------ */
+
+/* Fit w on the samples t in [t0, t1).
+ *   states    T x N float32 (row t = the states sampled after input sample
+ *             t, as sto_run writes them), host or device; only rows
+ *             [t0, t1) are read.
+ *   y         T float64 targets, host or device (rows [t0, t1) are read).
+ *   beta_rel  >= 0 (0: plain least squares).
+ *   w_out     N + 1 float64 weights (bias last), host or device.
+ * Limits: 1 <= N <= 32768 (STO_ENOTSUP beyond), 0 <= t0 < t1 <= T.
+ * Errors: STO_EINVAL, STO_ENOTSUP, STO_ENONFINITE (NaN or Inf in the rows
+ *         or targets), STO_ESINGULAR (the system is not positive definite,
+ *         e.g. beta_rel = 0 with fewer samples than features), STO_ENOMEM,
+ *         STO_ECUDA. */
+STO_API int sto_readout_fit(const float* states, int64_t T, int64_t N, const double* y, int64_t t0,
+                            int64_t t1, double beta_rel, double* w_out, void* stream);
+
+/* y_hat[t] = sum_k states[t*N + k] w[k] + w[N] for every t in [0, T), in
+ * FP64.  states: T x N float32, w: N + 1 float64, y_hat: T float64; each host
+ * or device.  Errors: STO_EINVAL, STO_ENOTSUP, STO_ENOMEM, STO_ECUDA. */
+STO_API int sto_readout_predict(const float* states, int64_t T, int64_t N, const double* w,
+                                double* y_hat, void* stream);
+
+/* Normalised mean squared error of the readout w on the samples [t0, t1):
+ *     *nmse = mean_t (y_hat_t - y_t)^2 / var_t(y_t)
+ * (population variance over the same samples).  states, w, y as above;
+ * nmse is a host pointer.  Errors: STO_EINVAL (also for a constant target),
+ * STO_ENOTSUP, STO_ENOMEM, STO_ECUDA. */
+STO_API int sto_readout_nmse(const float* states, int64_t T, int64_t N, const double* w, const double* y,
+                             int64_t t0, int64_t t1, double* nmse, void* stream);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "sto.h"
+#include "readout.cuh"
 #include "sto_kernel.cuh"
 #include "stepper_plan.h"
 #include "sweep.cuh"
@@ -504,7 +505,11 @@ int finish_launch(sto_handle* h) {
 // group never pays for it), time a short launch (zero input, at most 50 RK4
 // steps) in each candidate block of the pool, the best of three, keep the
 // fastest, and restore the state.  Placement changes no arithmetic: the
-// results are the same bits.
+// results are the same bits.  Placement only changes speed, so a trial that
+// cannot run (no memory for the saved state, a trial launch that fails or
+// times out on a busy device) leaves the first placement in use, untimed,
+// and the caller's run goes ahead; only a failure to restore the state
+// fails the call.
 int tune_xbuf(sto_handle* h) {
   if (!h->xbuf_pending) return STO_OK;
   h->xbuf_pending = false;
@@ -523,7 +528,7 @@ int tune_xbuf(sto_handle* h) {
           cudaSuccess) {
     cudaGetLastError();
     cleanup();
-    return STO_ENOMEM;
+    return STO_OK;  // no trials: the first placement stays
   }
   cudaError_t e;
   if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
@@ -565,15 +570,22 @@ int tune_xbuf(sto_handle* h) {
   }
   h->params.substeps = substeps;
   h->inject_cta = inject;
-  h->d_xbuf = h->d_xbuf_pool + best * (h->xbuf_stride / sizeof(unsigned long long));
   if (rc == STO_OK) {
     h->xbuf_slot = best;
     h->xbuf_timed = h->xbuf_n;
+  } else {
+    // a failed trial decides nothing: first placement, not timed
+    best = 0;
+    h->xbuf_slot = 0;
+    h->xbuf_timed = 0;
+    cudaGetLastError();
   }
+  h->d_xbuf = h->d_xbuf_pool + best * (h->xbuf_stride / sizeof(unsigned long long));
   // back to the state before the trial launches
+  rc = STO_OK;
   if ((e = cudaMemcpyAsync(h->d_state, saved, sbytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-    if (rc == STO_OK) rc = cuda_fail(e);
+    rc = cuda_fail(e);
   cleanup();
   return rc;
 }
@@ -827,6 +839,7 @@ const char* sto_strerror(int code) {
     case STO_ENONFINITE: base = "non-finite input"; break;
     case STO_ENOTSUP: base = "size or option not supported by the library"; break;
     case STO_ETOOBIG: base = "size exceeds the static scratch of sto_run_noalloc (N <= 16384)"; break;
+    case STO_ESINGULAR: base = "the ridge system is not positive definite"; break;
     default: break;
   }
   if (code == STO_ECUDA && g_last_cuda != cudaSuccess)
@@ -2033,6 +2046,204 @@ void sto_batch_destroy(sto_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   free_batch(b);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- readout
+//
+// Ridge readout on the GPU (readout.cuh): Gram matrix, ridge shift, blocked
+// Cholesky with the forward substitution folded in, back substitution.  The
+// scratch (the (N + 2)^2 FP64 Gram matrix, copies of host inputs) is
+// allocated per call and freed before it returns.
+
+namespace {
+
+// Device memory freed when it goes out of scope.
+struct ScopedDev {
+  void* p = nullptr;
+  ScopedDev() = default;
+  ScopedDev(const ScopedDev&) = delete;
+  ScopedDev& operator=(const ScopedDev&) = delete;
+  ~ScopedDev() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t bytes) {
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return STO_ENOMEM;
+    }
+    return STO_OK;
+  }
+};
+
+// A device pointer to `bytes` of src (host or device): device memory is used
+// in place, host memory is copied into tmp on stream s.
+int device_input(const void* src, size_t bytes, cudaStream_t s, ScopedDev* tmp, const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return STO_OK;
+  }
+  if (const int rc = tmp->alloc(bytes)) return rc;
+  STO_CUDA(cudaMemcpyAsync(tmp->p, src, bytes, cudaMemcpyHostToDevice, s));
+  *out = tmp->p;
+  return STO_OK;
+}
+
+constexpr int64_t kReadoutMaxN = 32768;  // the Gram matrix is (N + 2)^2 doubles (8.6 GB here)
+
+int readout_check(const float* states, int64_t T, int64_t N, int64_t t0, int64_t t1) {
+  if (!states || T < 1 || N < 1 || t0 < 0 || t1 > T || t1 <= t0) return STO_EINVAL;
+  if (N > kReadoutMaxN) return STO_ENOTSUP;
+  return STO_OK;
+}
+
+// flag: any non-finite value among n floats (device) or nd doubles (device).
+int readout_nonfinite(const float* d_f, long long n, const double* d_d, long long nd, cudaStream_t s,
+                      int* d_flag, bool* bad) {
+  STO_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  if (n > 0) {
+    const long long b = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    sto::nonfinite_kernel<<<static_cast<unsigned>(b), 256, 0, s>>>(d_f, n, d_flag);
+    STO_CUDA(cudaGetLastError());
+  }
+  if (nd > 0) {
+    const long long b = (nd + 255) / 256 < 4096 ? (nd + 255) / 256 : 4096;
+    sto::nonfinite_f64_kernel<<<static_cast<unsigned>(b), 256, 0, s>>>(d_d, nd, d_flag);
+    STO_CUDA(cudaGetLastError());
+  }
+  int h = 0;
+  STO_CUDA(cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  *bad = h != 0;
+  return STO_OK;
+}
+
+// y_hat (m doubles, device) of the m state rows at d_rows (device).
+int readout_predict_dev(const float* d_rows, int64_t m, int64_t N, const double* d_w, double* d_yhat,
+                        cudaStream_t s) {
+  const int64_t blocks = (m + 7) / 8;
+  sto::readout::predict_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(d_rows, N, static_cast<int>(N), m,
+                                                                             d_w, d_yhat);
+  STO_CUDA(cudaGetLastError());
+  return STO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sto_readout_fit(const float* states, int64_t T, int64_t N, const double* y, int64_t t0, int64_t t1,
+                    double beta_rel, double* w_out, void* stream) {
+  if (int rc = readout_check(states, T, N, t0, t1)) return rc;
+  if (!y || !w_out || !std::isfinite(beta_rel) || beta_rel < 0.0) return STO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t m = t1 - t0, n = N + 1, nr = N + 2;
+  int rc;
+  // rows [t0, t1) of the states and the target, on the device
+  ScopedDev t_states, t_y, t_gram, t_misc, t_w;
+  const void* pv = nullptr;
+  if ((rc = device_input(states + t0 * N, static_cast<size_t>(m * N) * 4, s, &t_states, &pv))) return rc;
+  const float* d_rows = static_cast<const float*>(pv);
+  if ((rc = device_input(y + t0, static_cast<size_t>(m) * 8, s, &t_y, &pv))) return rc;
+  const double* d_y = static_cast<const double*>(pv);
+  if ((rc = t_gram.alloc(static_cast<size_t>(nr) * nr * 8))) return rc;
+  if ((rc = t_misc.alloc(64))) return rc;
+  double* d_G = static_cast<double*>(t_gram.p);
+  int* d_status = static_cast<int*>(t_misc.p);
+  int* d_flag = d_status + 1;
+  double* d_beta = static_cast<double*>(t_misc.p) + 1;
+  double* d_w = w_out;
+  if (!is_device_ptr(w_out)) {
+    if ((rc = t_w.alloc(static_cast<size_t>(n) * 8))) return rc;
+    d_w = static_cast<double*>(t_w.p);
+  }
+  bool bad = false;
+  if ((rc = readout_nonfinite(d_rows, m * N, d_y, m, s, d_flag, &bad))) return rc;
+  if (bad) return STO_ENONFINITE;
+
+  using namespace sto::readout;
+  const int nri = static_cast<int>(nr), ni = static_cast<int>(n);
+  const unsigned gt = static_cast<unsigned>((nr + kGramTile - 1) / kGramTile);
+  gram_kernel<<<dim3(gt, gt), 256, 0, s>>>(d_rows, N, d_y, static_cast<int>(N), 0, m, d_G);
+  STO_CUDA(cudaGetLastError());
+  ridge_shift_kernel<<<1, 1024, 0, s>>>(d_G, nri, ni, beta_rel, d_beta);
+  STO_CUDA(cudaGetLastError());
+  STO_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  for (int k0 = 0; k0 < ni; k0 += kCholB) {
+    const int kb = ni - k0 < kCholB ? ni - k0 : kCholB;
+    chol_diag_kernel<<<1, kCholB * kCholB, 0, s>>>(d_G, nri, k0, kb, d_status);
+    STO_CUDA(cudaGetLastError());
+    const int below = nri - k0 - kb;  // rows under the diagonal block, the target row included
+    if (below > 0) {
+      chol_panel_kernel<<<static_cast<unsigned>((below + 255) / 256), 256, 0, s>>>(d_G, nri, nri, k0, kb,
+                                                                                   d_status);
+      STO_CUDA(cudaGetLastError());
+      const unsigned ut = static_cast<unsigned>((below + kUpdTile - 1) / kUpdTile);
+      chol_update_kernel<<<dim3(ut, ut), 256, 0, s>>>(d_G, nri, nri, k0, kb, d_status);
+      STO_CUDA(cudaGetLastError());
+    }
+  }
+  back_solve_kernel<<<1, 1024, 0, s>>>(d_G, nri, nri, ni, d_w, d_status);
+  STO_CUDA(cudaGetLastError());
+  int status = 0;
+  STO_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (d_w != w_out) STO_CUDA(cudaMemcpyAsync(w_out, d_w, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  return status ? STO_ESINGULAR : STO_OK;
+}
+
+int sto_readout_predict(const float* states, int64_t T, int64_t N, const double* w, double* y_hat,
+                        void* stream) {
+  if (int rc = readout_check(states, T, N, 0, T)) return rc;
+  if (!w || !y_hat) return STO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc;
+  ScopedDev t_states, t_w, t_out;
+  const void* pv = nullptr;
+  if ((rc = device_input(states, static_cast<size_t>(T * N) * 4, s, &t_states, &pv))) return rc;
+  const float* d_rows = static_cast<const float*>(pv);
+  if ((rc = device_input(w, static_cast<size_t>(N + 1) * 8, s, &t_w, &pv))) return rc;
+  const double* d_w = static_cast<const double*>(pv);
+  double* d_out = y_hat;
+  if (!is_device_ptr(y_hat)) {
+    if ((rc = t_out.alloc(static_cast<size_t>(T) * 8))) return rc;
+    d_out = static_cast<double*>(t_out.p);
+  }
+  if ((rc = readout_predict_dev(d_rows, T, N, d_w, d_out, s))) return rc;
+  if (d_out != y_hat) STO_CUDA(cudaMemcpyAsync(y_hat, d_out, static_cast<size_t>(T) * 8, cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  return STO_OK;
+}
+
+int sto_readout_nmse(const float* states, int64_t T, int64_t N, const double* w, const double* y, int64_t t0,
+                     int64_t t1, double* nmse, void* stream) {
+  if (int rc = readout_check(states, T, N, t0, t1)) return rc;
+  if (!w || !y || !nmse) return STO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t m = t1 - t0;
+  int rc;
+  ScopedDev t_states, t_w, t_y, t_yhat, t_out;
+  const void* pv = nullptr;
+  if ((rc = device_input(states + t0 * N, static_cast<size_t>(m * N) * 4, s, &t_states, &pv))) return rc;
+  const float* d_rows = static_cast<const float*>(pv);
+  if ((rc = device_input(w, static_cast<size_t>(N + 1) * 8, s, &t_w, &pv))) return rc;
+  const double* d_w = static_cast<const double*>(pv);
+  if ((rc = device_input(y + t0, static_cast<size_t>(m) * 8, s, &t_y, &pv))) return rc;
+  const double* d_y = static_cast<const double*>(pv);
+  if ((rc = t_yhat.alloc(static_cast<size_t>(m) * 8)) || (rc = t_out.alloc(16))) return rc;
+  double* d_yhat = static_cast<double*>(t_yhat.p);
+  double* d_out = static_cast<double*>(t_out.p);
+  if ((rc = readout_predict_dev(d_rows, m, N, d_w, d_yhat, s))) return rc;
+  sto::readout::nmse_kernel<<<1, 1024, 0, s>>>(d_yhat, d_y, 0, m, d_out);
+  STO_CUDA(cudaGetLastError());
+  double h[2] = {0.0, 0.0};
+  STO_CUDA(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STO_CUDA(cudaStreamSynchronize(s));
+  if (!(h[1] > 0.0)) return STO_EINVAL;  // a constant target has no normalised error
+  *nmse = h[0] / h[1];
+  return STO_OK;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_PKG, "libsto.so")
 STO_OK, STO_EINVAL, STO_ENOMEM, STO_ECUDA, STO_ETIMEOUT, STO_ENONFINITE, STO_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6)
 STO_ETOOBIG = -7
+STO_ESINGULAR = -8
 STO_PRODUCT_DF, STO_PRODUCT_F64 = 1, 2
 # coupling precision of a Reservoir -> product of sto_create_f64 (None: FP32 sto_create)
 COUPLINGS = {"f32": None, "df64": STO_PRODUCT_DF, "f64": STO_PRODUCT_F64}
@@ -116,6 +117,10 @@ SIGNATURES = {
     "sto_group_run": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_group_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sto_group_destroy": (None, [_VP]),
+    "sto_readout_fit": (ctypes.c_int, [_VP, _I64, _I64, _VP, _I64, _I64, ctypes.c_double, _VP, _VP]),
+    "sto_readout_predict": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _VP]),
+    "sto_readout_nmse": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _I64, _I64,
+                                        ctypes.POINTER(ctypes.c_double), _VP]),
 }
 
 _lib = None
@@ -400,6 +405,18 @@ def sto_run_noalloc(N, params: Params, W, w_in, state, u, T, states_out=None, st
     memory (pool-owned devices, capture-free real-time loops, plug-ins).
     All arrays are caller-owned CUDA tensors: W (N x N float32), w_in, state
     (3 x N float64, advanced in place), u, states_out (or None)."""
+    # the library reads and writes these arrays in place and cannot see their
+    # extents: check them here, before any kernel touches them
+    N, T = int(N), int(T)
+    sizes = {"W": (W, N * N, N * N), "w_in": (w_in, N * params.n_in, N * params.n_in),
+             "state": (state, 3 * N, 3 * N), "u": (u, T * params.n_in, None)}
+    if states_out is not None:
+        sizes["states_out"] = (states_out, T * N, None)
+    for name, (a, need, exact) in sizes.items():
+        n = int(np.prod(a.shape))
+        if n < need or (exact is not None and n != exact):
+            raise ValueError(f"{name} holds {n} values; sto_run_noalloc(N={N}, T={T}, "
+                             f"n_in={params.n_in}) needs {'exactly ' if exact is not None else ''}{need}")
     cp = params.to_c()
     pW, kW = _ptr(W, np.float32)
     pwin, kwin = _ptr(w_in, np.float32)
@@ -408,6 +425,101 @@ def sto_run_noalloc(N, params: Params, W, w_in, state, u, T, states_out=None, st
     pso, kso = _ptr(states_out, np.float32)
     _check(load_library().sto_run_noalloc(N, ctypes.byref(cp), pW, pwin, pst, pu, T, pso,
                                           _stream_ptr(stream)))
+
+
+def _states_2d(states):
+    if len(states.shape) != 2:
+        raise ValueError("states must be T x N")
+    return int(states.shape[0]), int(states.shape[1])
+
+
+def _out_f64(out, n):
+    """(pointer, keepalive, array) of a float64 output of n elements: a given
+    contiguous float64 numpy array or torch tensor, or a new numpy array."""
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    if hasattr(out, "data_ptr"):
+        p, k = _ptr(out, np.float64)
+    elif isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous:
+        p, k = out.ctypes.data, out
+    else:
+        raise TypeError("outputs must be contiguous float64 arrays")
+    if int(np.prod(out.shape)) != n:
+        raise ValueError(f"output must hold {n} values")
+    return p, k, out
+
+
+def sto_readout_fit(states, y, t0, t1, beta_rel=1e-6, w_out=None, stream=None):
+    """Ridge readout with bias fitted on rows [t0, t1) of states (T x N float32)
+    against y (T float64); returns the N + 1 weights (bias last) in w_out
+    (numpy or torch float64, host or device; a new numpy array if None)."""
+    T, N = _states_2d(states)
+    if int(np.prod(y.shape)) != T:
+        raise ValueError("y must hold one target per state row")
+    ps, ks = _ptr(states, np.float32)
+    py, ky = _ptr(y, np.float64)
+    pw, kw, w = _out_f64(w_out, N + 1)
+    _check(load_library().sto_readout_fit(ps, T, N, py, int(t0), int(t1), float(beta_rel), pw,
+                                          _stream_ptr(stream)))
+    return w
+
+
+def sto_readout_predict(states, w, y_hat=None, stream=None):
+    """y_hat[t] = states[t] . w[:N] + w[N] in FP64 (a new numpy array if y_hat is None)."""
+    T, N = _states_2d(states)
+    if int(np.prod(w.shape)) != N + 1:
+        raise ValueError("w must hold N + 1 weights")
+    ps, ks = _ptr(states, np.float32)
+    pw, kw = _ptr(w, np.float64)
+    po, ko, out = _out_f64(y_hat, T)
+    _check(load_library().sto_readout_predict(ps, T, N, pw, po, _stream_ptr(stream)))
+    return out
+
+
+def sto_readout_nmse(states, w, y, t0, t1, stream=None) -> float:
+    """mean((y_hat - y)^2) / var(y) over rows [t0, t1)."""
+    T, N = _states_2d(states)
+    if int(np.prod(w.shape)) != N + 1 or int(np.prod(y.shape)) != T:
+        raise ValueError("w must hold N + 1 weights and y one target per state row")
+    ps, ks = _ptr(states, np.float32)
+    pw, kw = _ptr(w, np.float64)
+    py, ky = _ptr(y, np.float64)
+    out = ctypes.c_double()
+    _check(load_library().sto_readout_nmse(ps, T, N, pw, py, int(t0), int(t1), ctypes.byref(out),
+                                           _stream_ptr(stream)))
+    return out.value
+
+
+def delay_target(u, delay: int = 5) -> np.ndarray:
+    """The recall target y_t = u_{t - delay} of the first input channel (0 for
+    t < delay), as float64 on the host: an index shift of the input series."""
+    if hasattr(u, "detach"):
+        u = u.detach().cpu().numpy()
+    u = np.asarray(u, dtype=np.float64).reshape(len(u), -1)[:, 0]
+    y = np.zeros_like(u)
+    if delay > 0:
+        y[delay:] = u[:-delay]
+    else:
+        y[:] = u
+    return y
+
+
+def readout_split(T: int, washout: int):
+    """(train, test) sample ranges after the washout: the first half of the
+    remaining samples trains the readout, the second half scores it."""
+    n = T - washout
+    if n < 4:
+        raise ValueError("too few samples after the washout")
+    half = washout + n // 2
+    return (washout, half), (half, T)
+
+
+def readout_evaluate(states, y, washout: int = 100, beta_rel: float = 1e-6, stream=None):
+    """Fit on the first half after the washout, score on the second half:
+    returns (w, nmse_test)."""
+    (a, b), (c, d) = readout_split(int(states.shape[0]), washout)
+    w = sto_readout_fit(states, y, a, b, beta_rel, stream=stream)
+    return w, sto_readout_nmse(states, w, y, c, d, stream=stream)
 
 
 def sto_strerror(code: int) -> str:

@@ -44,10 +44,11 @@ def test_exports_are_only_the_abi():
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.sto_abi_version() == 2
-    for code in [0, -1, -2, -3, -4, -5, -6]:
+    assert lib.sto_abi_version() == 3
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
         assert sto.sto_strerror(code)
     assert "invalid" in sto.sto_strerror(-1)
+    assert "positive definite" in sto.sto_strerror(sto.STO_ESINGULAR)
 
 
 def test_default_params_are_the_paper_table(lib):
@@ -119,3 +120,24 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     for N, R in ((32769, 1), (1, 65537), (20000, 30000)):
         assert lib.sto_batch_create(N, R, ctypes.byref(cp), None, None, buf, buf, None, None,
                                     ctypes.byref(b)) == sto.STO_ENOTSUP, (N, R)
+
+
+def test_noalloc_wrapper_checks_extents_before_the_call(lib):
+    """sto_run_noalloc reads and writes caller arrays in place and the C side
+    cannot see their extents: the binding rejects short or mis-sized arrays
+    with ValueError before the library is called (no GPU needed)."""
+    import numpy as np
+    N, T = 8, 3
+    P = sto.Params(n_in=2)
+    ok = {"W": np.zeros(N * N, np.float32), "w_in": np.zeros(N * 2, np.float32),
+          "state": np.zeros(3 * N), "u": np.zeros(T * 2, np.float32),
+          "states_out": np.zeros(T * N, np.float32)}
+    bad = {"W": np.zeros(N * N - 1, np.float32), "w_in": np.zeros(N, np.float32),
+           "state": np.zeros(3 * N + 1), "u": np.zeros(T * 2 - 1, np.float32),
+           "states_out": np.zeros(T * N - 1, np.float32)}
+    for name in ok:
+        args = dict(ok)
+        args[name] = bad[name]
+        with pytest.raises(ValueError, match=name):
+            sto.sto_run_noalloc(N, P, args["W"], args["w_in"], args["state"], args["u"], T,
+                                args["states_out"])

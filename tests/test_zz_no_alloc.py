@@ -3,16 +3,17 @@ allocate device memory (a framework's pool allocator owns the device, a
 real-time loop cannot afford cudaMalloc's implicit synchronisation, or a
 plug-in may only use the buffers it is given).
 
-It is checked through the C ABI against the handle-based sto_run on the same
-inputs, over two consecutive calls that continue from the state the first
-one left, with the tolerance the other parity tests use (1e-5).  The file is
-named to be collected last, and it passes alone in a fresh process as well
-as after the other tests.
+It is checked through the C ABI against the handle-based sto_run and against
+the FP64 oracle on the same inputs, over two consecutive calls that continue
+from the state the first one left, with the tolerance the other parity tests
+use (1e-5), and a call after the first must leave the device's free memory
+unchanged.  The file is named to be collected last, and it passes alone in a
+fresh process as well as after the other tests.
 """
 import numpy as np
 import pytest
 
-from helpers import make_system
+from helpers import make_system, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -58,15 +59,45 @@ def test_noalloc_matches_sto_run_on_two_calls(sto, N):
     assert torch.max(torch.abs(out2 - ref2)).item() <= 1e-5
     assert np.max(np.abs(state.cpu().numpy() - m_ref)) <= 1e-5
 
+    # and against the FP64 oracle over the same five samples
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    got = np.vstack([out1.cpu().numpy(), out2.cpu().numpy()])
+    assert np.max(np.abs(got - st_orc)) <= 1e-5
+    assert np.max(np.abs(state.cpu().numpy() - m_orc)) <= 1e-5
+
+
+def test_noalloc_call_allocates_no_device_memory(sto):
+    """After the first call on the device (which looks up the static array),
+    a call leaves the device's free memory exactly as it was."""
+    N, T = 1000, 2
+    W, w_in, m0, u = make_system(N, "gauss", seed=22, T=T)
+    P = sto.Params(substeps=3, A_cp=50.0)
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    Wd, wd, ud = torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), torch.from_numpy(u).to(dev)
+    state = torch.from_numpy(m0.astype(np.float64)).to(dev)
+    out = torch.zeros((T, N), dtype=torch.float32, device=dev)
+    sto.sto_run_noalloc(N, P, Wd, wd, state, ud, T, out, stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        sto.sto_run_noalloc(N, P, Wd, wd, state, ud, T, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(sto):
-    P = sto.Params()
+    """The library's own checks, called through the C ABI directly (the Python
+    binding would already refuse these arrays for their extents)."""
+    import ctypes
+    lib = sto.load_library()
+    cp = sto.Params().to_c()
     dev = torch.device("cuda")
     tiny = torch.zeros(16, dtype=torch.float32, device=dev)
     st = torch.zeros(3 * 16, dtype=torch.float64, device=dev)
-    with pytest.raises(sto.StoError) as e:
-        sto.sto_run_noalloc(16388, P, tiny, tiny, st, tiny, 1, None)
-    assert e.value.code == sto.STO_ETOOBIG
-    with pytest.raises(sto.StoError) as e:      # N must be a multiple of 4
-        sto.sto_run_noalloc(6, P, tiny, tiny, st, tiny, 1, None)
-    assert e.value.code == sto.STO_EINVAL
+    p = tiny.data_ptr()
+    assert lib.sto_run_noalloc(16388, ctypes.byref(cp), p, p, st.data_ptr(), p, 1, None,
+                               None) == sto.STO_ETOOBIG
+    # N must be a multiple of 4
+    assert lib.sto_run_noalloc(6, ctypes.byref(cp), p, p, st.data_ptr(), p, 1, None,
+                               None) == sto.STO_EINVAL
