@@ -520,6 +520,68 @@ STO_API int sto_readout_predict(const float* states, int64_t T, int64_t N, const
 STO_API int sto_readout_nmse(const float* states, int64_t T, int64_t N, const double* w, const double* y,
                              int64_t t0, int64_t t1, double* nmse, void* stream);
 
+/* ------------------------------------------------------------------------
+ * One reservoir split across GPUs by rows.  The coupling of Eq. (coup) is
+ * the matrix-vector product W m^x (Sec. 3.3): the GPU that holds rows
+ * [row0, row0 + rows) of W advances exactly those oscillators, and per RK4
+ * stage needs only the stage values m^x of all N oscillators, which the
+ * GPUs exchange between stages (an all-gather of N floats; the caller's
+ * collective, e.g. NCCL, on the same stream).  A run is
+ *     sto_shard_publish(own x) ; all-gather into x
+ *     for every input sample t, RK4 step j < substeps, stage s < 4:
+ *         sto_shard_stage(x, s, u_t, flags, own x', states_row) ; all-gather x' into x
+ * with flags = STO_SHARD_SAMPLE_START at (j = 0, s = 0) and
+ * STO_SHARD_SAMPLE_END at (j = substeps - 1, s = 3).  Results equal those
+ * of sto_run on the whole reservoir up to the order of the FP32 row sums
+ * (the same double-float torque and RK4 combination).
+ * ------------------------------------------------------------------------ */
+typedef struct sto_shard sto_shard; /* opaque */
+
+#define STO_SHARD_SAMPLE_START 1  /* form the input field of the block from u_t first */
+#define STO_SHARD_SAMPLE_END 2    /* write the sampled component after stage 3 */
+
+/* Create the block [row0, row0 + rows) of a reservoir of N oscillators on the
+ * current device.
+ *   params     as for sto_create (the same on every block).
+ *   W_rows     rows x N float32 (rows row0 .. row0 + rows - 1 of W), host or
+ *              device; copied.
+ *   w_in_rows  rows x n_in float32, host or device; copied.
+ *   m0_rows    3 x rows float32 (m^x block, m^y block, m^z block of these
+ *              oscillators), host or device, or NULL for Eq. (initial).
+ *   stream     cudaStream_t of every launch of the block.
+ * Errors: STO_EINVAL (sizes: 0 <= row0, 1 <= rows, row0 + rows <= N),
+ *         STO_ENONFINITE, STO_ENOTSUP, STO_ENOMEM, STO_ECUDA. */
+STO_API int sto_shard_create(int64_t N, int64_t row0, int64_t rows, const sto_params* params,
+                             const float* W_rows, const float* w_in_rows, const float* m0_rows,
+                             void* stream, sto_shard** out);
+
+/* Write the block's stage values for the first stage of a run (m^x of the
+ * current state, FP32) to x_rows (rows floats, device).  Asynchronous.
+ * Errors: STO_EINVAL, STO_ECUDA. */
+STO_API int sto_shard_publish(sto_shard* h, float* x_rows);
+
+/* Finish RK4 stage `stage` (0..3) for the block and write its next stage
+ * values to x_next (rows floats, device).
+ *   x           the stage values m^x of all N oscillators in oscillator order
+ *               (device, 16-byte aligned; entries past N are ignored).
+ *   u_t         the input sample (n_in floats, device); read only with
+ *               STO_SHARD_SAMPLE_START (allowed at stage 0 only).
+ *   flags       STO_SHARD_SAMPLE_START | STO_SHARD_SAMPLE_END (stage 3 only).
+ *   states_row  rows floats (device) or NULL: the sampled component after
+ *               stage 3 when STO_SHARD_SAMPLE_END is set.
+ * One kernel launch on the block's stream; no synchronisation, no waits on
+ * other blocks.  Errors (argument checks only): STO_EINVAL, STO_ECUDA. */
+STO_API int sto_shard_stage(sto_shard* h, const float* x, int32_t stage, const float* u_t, int32_t flags,
+                            float* x_next, float* states_row);
+
+/* The block's state, 3 x rows doubles (host or device).  Synchronises.
+ * Errors: STO_EINVAL, STO_ENONFINITE (set), STO_ENOMEM, STO_ECUDA. */
+STO_API int sto_shard_set_state_f64(sto_shard* h, const double* m);
+STO_API int sto_shard_get_state_f64(const sto_shard* h, double* m);
+
+/* Release the block (NULL is allowed). */
+STO_API void sto_shard_destroy(sto_shard* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ SRC = [os.path.join(PKG, "csrc", "sto.cu")]
 DEPS = SRC + [os.path.join(PKG, "csrc", "sto_kernel.cuh"), os.path.join(PKG, "csrc", "dfloat.cuh"),
               os.path.join(PKG, "csrc", "stepper_plan.h"),
               os.path.join(PKG, "csrc", "sweep.cuh"), os.path.join(PKG, "csrc", "readout.cuh"),
+              os.path.join(PKG, "csrc", "shard.cuh"),
               os.path.join(ROOT, "include", "sto.h")]
 LIB = os.path.join(PKG, "libsto.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

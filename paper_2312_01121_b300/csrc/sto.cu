@@ -22,6 +22,7 @@
 
 #include "sto.h"
 #include "readout.cuh"
+#include "shard.cuh"
 #include "sto_kernel.cuh"
 #include "stepper_plan.h"
 #include "sweep.cuh"
@@ -2244,6 +2245,194 @@ int sto_readout_nmse(const float* states, int64_t T, int64_t N, const double* w,
   if (!(h[1] > 0.0)) return STO_EINVAL;  // a constant target has no normalised error
   *nmse = h[0] / h[1];
   return STO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- row shards
+//
+// One row block of a reservoir split across GPUs (shard.cuh).  The handle
+// owns, on the device current at creation, the block's rows of W (padded to
+// a multiple of 4 columns), its input weights, its double-float state and
+// input field.  Stages are launched one at a time by the caller, who
+// exchanges the stage values between launches.
+
+struct sto_shard {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t N = 0, row0 = 0, rows = 0, ld = 0;
+  sto_params params{};
+  float* d_W = nullptr;
+  float* d_win = nullptr;
+  float2* d_st = nullptr;  // mn | ms | ks ([3][rows] each), hin [rows]
+  int* d_flag = nullptr;
+  sto::ShardArgs args{};
+};
+
+namespace {
+
+void free_shard(sto_shard* h) {
+  if (!h) return;
+  cudaFree(h->d_W);
+  cudaFree(h->d_win);
+  cudaFree(h->d_st);
+  cudaFree(h->d_flag);
+  delete h;
+}
+
+int shard_set_state_host(sto_shard* h, const double* m) {
+  const int n = static_cast<int>(3 * h->rows);
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(m[i])) return STO_ENONFINITE;
+  ScopedDev tmp;
+  if (const int rc = tmp.alloc(static_cast<size_t>(n) * 8)) return rc;
+  STO_CUDA(cudaMemcpyAsync(tmp.p, m, static_cast<size_t>(n) * 8, cudaMemcpyHostToDevice, h->stream));
+  sto::shard_state_in_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(static_cast<const double*>(tmp.p), n,
+                                                                      h->d_st);
+  STO_CUDA(cudaGetLastError());
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return STO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sto_shard_create(int64_t N, int64_t row0, int64_t rows, const sto_params* params, const float* W_rows,
+                     const float* w_in_rows, const float* m0_rows, void* stream, sto_shard** out) {
+  if (!out) return STO_EINVAL;
+  *out = nullptr;
+  if (N < 1 || row0 < 0 || rows < 1 || row0 + rows > N || !W_rows || !w_in_rows) return STO_EINVAL;
+  if (int rc = check_params(params)) return rc;
+  if (N > (1LL << 24) || rows * N > (1LL << 34)) return STO_ENOTSUP;
+  sto_shard* h = new (std::nothrow) sto_shard();
+  if (!h) return STO_ENOMEM;
+  h->N = N;
+  h->row0 = row0;
+  h->rows = rows;
+  h->ld = (N + 3) / 4 * 4;
+  h->params = *params;
+  h->stream = static_cast<cudaStream_t>(stream);
+  auto fail = [&](int code) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_shard(h);
+    return code;
+  };
+  if (const cudaError_t e = cudaGetDevice(&h->device)) return fail(cuda_fail(e));
+  const int n_in = params->n_in;
+  const size_t w_elems = static_cast<size_t>(rows) * N, win_elems = static_cast<size_t>(rows) * n_in;
+  if (cudaMalloc(&h->d_W, static_cast<size_t>(rows) * h->ld * 4) != cudaSuccess ||
+      cudaMalloc(&h->d_win, win_elems * 4) != cudaSuccess ||
+      cudaMalloc(&h->d_st, static_cast<size_t>(10) * rows * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&h->d_flag, 16) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(STO_ENOMEM);
+  }
+  int rc;
+  {
+    ScopedDev tw;
+    const void* pv = nullptr;
+    if ((rc = device_input(W_rows, w_elems * 4, h->stream, &tw, &pv))) return fail(rc);
+    const float* dW = static_cast<const float*>(pv);
+    bool bad = false;
+    if ((rc = readout_nonfinite(dW, static_cast<long long>(w_elems), nullptr, 0, h->stream, h->d_flag, &bad)))
+      return fail(rc);
+    if (bad) return fail(STO_ENONFINITE);
+    const long long total = rows * h->ld;
+    const unsigned blocks = static_cast<unsigned>((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    sto::shard_pad_w_kernel<<<blocks, 256, 0, h->stream>>>(dW, static_cast<int>(rows), static_cast<int>(N),
+                                                           static_cast<int>(h->ld), h->d_W);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  }
+  if (const cudaError_t e = cudaMemcpyAsync(h->d_win, w_in_rows, win_elems * 4, cudaMemcpyDefault, h->stream))
+    return fail(cuda_fail(e));
+  {
+    bool bad = false;
+    if ((rc = readout_nonfinite(h->d_win, static_cast<long long>(win_elems), nullptr, 0, h->stream, h->d_flag,
+                                &bad)))
+      return fail(rc);
+    if (bad) return fail(STO_ENONFINITE);
+  }
+  std::vector<double> m(3 * static_cast<size_t>(rows));
+  if (m0_rows) {
+    std::vector<float> mf;
+    if ((rc = fetch_floats(&mf, m0_rows, m.size(), h->stream))) return fail(rc);
+    for (size_t i = 0; i < m.size(); ++i) m[i] = mf[i];
+  } else {
+    const double phi0 = 2.0 * M_PI / 360.0;  // Eq. (initial)
+    for (int64_t k = 0; k < rows; ++k) {
+      m[k] = std::sin(phi0) * std::cos(phi0);
+      m[rows + k] = std::sin(phi0) * std::sin(phi0);
+      m[2 * rows + k] = std::cos(phi0);
+    }
+  }
+  if (const cudaError_t e = cudaMemsetAsync(h->d_st, 0, static_cast<size_t>(10) * rows * sizeof(float2), h->stream))
+    return fail(cuda_fail(e));
+  if ((rc = shard_set_state_host(h, m.data()))) return fail(rc);
+  sto::ShardArgs& a = h->args;
+  a.W = h->d_W;
+  a.w_in = h->d_win;
+  a.mn = h->d_st;
+  a.ms = h->d_st + 3 * rows;
+  a.ks = h->d_st + 6 * rows;
+  a.hin = h->d_st + 9 * rows;
+  a.N = static_cast<int>(N);
+  a.ld = static_cast<int>(h->ld);
+  a.rows = static_cast<int>(rows);
+  a.n_in = n_in;
+  a.comp = params->sample_component;
+  set_constants(*params, &a.c);
+  *out = h;
+  return STO_OK;
+}
+
+int sto_shard_publish(sto_shard* h, float* x_rows) {
+  if (!h || !x_rows || !is_device_ptr(x_rows)) return STO_EINVAL;
+  const int rows = static_cast<int>(h->rows);
+  sto::shard_publish_kernel<<<(rows + 255) / 256, 256, 0, h->stream>>>(h->d_st, rows, x_rows);
+  return cuda_rc(cudaGetLastError());
+}
+
+int sto_shard_stage(sto_shard* h, const float* x, int32_t stage, const float* u_t, int32_t flags, float* x_next,
+                    float* states_row) {
+  if (!h || !x || !x_next || stage < 0 || stage > 3 || (flags & ~3) != 0) return STO_EINVAL;
+  if ((flags & sto::kShardSampleStart) && (!u_t || stage != 0)) return STO_EINVAL;
+  if ((flags & sto::kShardSampleEnd) && stage != 3) return STO_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return STO_EINVAL;
+  if (!is_device_ptr(x) || !is_device_ptr(x_next) || (u_t && !is_device_ptr(u_t)) ||
+      (states_row && !is_device_ptr(states_row)))
+    return STO_EINVAL;
+  const unsigned blocks = static_cast<unsigned>((h->rows + 7) / 8);
+  sto::shard_stage_kernel<<<blocks, 256, 0, h->stream>>>(h->args, x, stage, u_t, flags, x_next, states_row);
+  return cuda_rc(cudaGetLastError());
+}
+
+int sto_shard_set_state_f64(sto_shard* h, const double* m) {
+  if (!h || !m) return STO_EINVAL;
+  std::vector<double> md(3 * static_cast<size_t>(h->rows));
+  STO_CUDA(cudaMemcpyAsync(md.data(), m, md.size() * 8, cudaMemcpyDefault, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return shard_set_state_host(h, md.data());
+}
+
+int sto_shard_get_state_f64(const sto_shard* h, double* m) {
+  if (!h || !m) return STO_EINVAL;
+  const int n = static_cast<int>(3 * h->rows);
+  ScopedDev tmp;
+  if (const int rc = tmp.alloc(static_cast<size_t>(n) * 8)) return rc;
+  sto::shard_state_out_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(h->d_st, n, static_cast<double*>(tmp.p));
+  STO_CUDA(cudaGetLastError());
+  STO_CUDA(cudaMemcpyAsync(m, tmp.p, static_cast<size_t>(n) * 8, cudaMemcpyDefault, h->stream));
+  STO_CUDA(cudaStreamSynchronize(h->stream));
+  return STO_OK;
+}
+
+void sto_shard_destroy(sto_shard* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_shard(h);
 }
 
 }  // extern "C"

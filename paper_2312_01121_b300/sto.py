@@ -121,6 +121,13 @@ SIGNATURES = {
     "sto_readout_predict": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _VP]),
     "sto_readout_nmse": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _I64, _I64,
                                         ctypes.POINTER(ctypes.c_double), _VP]),
+    "sto_shard_create": (ctypes.c_int, [_I64, _I64, _I64, ctypes.POINTER(sto_params), _VP, _VP, _VP, _VP,
+                                        ctypes.POINTER(_VP)]),
+    "sto_shard_publish": (ctypes.c_int, [_VP, _VP]),
+    "sto_shard_stage": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _VP]),
+    "sto_shard_set_state_f64": (ctypes.c_int, [_VP, _VP]),
+    "sto_shard_get_state_f64": (ctypes.c_int, [_VP, _VP]),
+    "sto_shard_destroy": (None, [_VP]),
 }
 
 _lib = None
