@@ -67,8 +67,9 @@ def parse():
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
     ap.add_argument("--group-lanes", type=int, default=0, help="lanes of the group launch (0 = auto)")
     ap.add_argument("--adj-n", type=int, default=1000)
-    ap.add_argument("--adj-t", type=int, default=40, help="input samples per adjoint call")
-    ap.add_argument("--adj-k", type=int, default=20, help="checkpoint interval (samples)")
+    ap.add_argument("--adj-t", type=int, default=2000, help="input samples per adjoint call")
+    ap.add_argument("--adj-k", type=int, default=100, help="checkpoint interval (samples)")
+    ap.add_argument("--adj-reps", type=int, default=1, help="timed adjoint calls")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-ns", default="1000,10000",
                     help="N of the FP64 replica of the paper's benchmark (comma separated)")
@@ -304,8 +305,10 @@ def time_adjoint(args, seed, torch, sto, dev):
                         m0=torch.from_numpy(m0).to(dev), stream=stream)
     u_d = torch.from_numpy(u).to(dev)
     g = torch.from_numpy(np.random.default_rng(seed).standard_normal((T, N)).astype(np.float32)).to(dev)
-    res.adjoint(u_d, g, K)  # warm-up (builds W^T, allocates the recording)
-    reps = 3
+    # warm-up on one checkpoint segment: builds W^T, allocates the recording
+    # (K samples), times the exchange-buffer placements
+    res.adjoint(u_d[:K], g[:K], K)
+    reps = max(1, args.adj_reps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -367,6 +370,7 @@ def time_sweep(args, seed, torch, sto, dev, peaks):
             "coupling_tflops_algorithmic": alg_flop / (us_stage * 1e-6) / 1e12,
             "coupling_tflops_executed": exe_flop / (us_stage * 1e-6) / 1e12,
             "tensor_peak_tflops": peaks.get("bf16"),
+            "tensor_peak_tflops_sustained": peaks.get("bf16_sustained"),
             "frac_of_bf16_peak_whole_stage": (exe_flop / (us_stage * 1e-6) / 1e12) / peaks["bf16"]
             if peaks.get("bf16") else None,
             # the per-pair RK4 state (mn, ms, ksum as double-float triples) is read and written
@@ -537,6 +541,38 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def summary(line, hbm_peak):
+    """The secondary workloads' headline numbers in one short object, printed
+    last in the line so that a truncated tail of the output still holds them."""
+    out = {"n1e4_us_per_stage": line["roofline"]["us_per_stage"],
+           "n1e4_frac_hbm_alg": line["roofline"]["frac"],
+           "n1e4_frac_hbm_dram": line["roofline"].get("frac_dram")}
+    also = line.get("also")
+    if also:
+        out.update({"n1e3_node_updates_per_s": also["value"], "n1e3_us_per_stage": also["us_per_stage"],
+                    "n1e3_hbm_equiv_us_per_stage": also["hbm_roofline_us_per_stage"]})
+    adj = line.get("adjoint")
+    if adj:
+        out.update({"adjoint_node_updates_per_s": adj["value"], "adjoint_s_per_call": adj["ms_per_call"] / 1e3,
+                    "adjoint_config": f"N={adj['N']} T={adj['input_samples']} K={adj['ckpt_every']}"})
+    sw = line.get("sweep")
+    if sw:
+        out.update({"sweep_us_per_stage": sw["us_per_stage"], "sweep_node_updates_per_s": sw["value"],
+                    "sweep_frac_bf16_alg": sw["coupling_tflops_algorithmic"] / sw["tensor_peak_tflops"],
+                    "sweep_frac_bf16_alg_sustained": sw["coupling_tflops_algorithmic"]
+                    / sw["tensor_peak_tflops_sustained"],
+                    "sweep_frac_bf16_exec": sw["frac_of_bf16_peak_whole_stage"]})
+    grp = line.get("group")
+    if grp:
+        out.update({"group_us_per_stage": grp["us_per_stage"], "group_frac_hbm": grp["frac_of_hbm"]})
+    fp = line.get("fp64")
+    if fp:
+        for c in fp["cases"]:
+            if c["N"] == 10000:
+                out[f"fp64_{c['coupling']}_n1e4_us_per_stage"] = c["us_per_stage"]
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -585,6 +621,7 @@ def main():
     mean_launch_s = statistics.mean(main_r["per_launch_ms"]) / 1e3
     achieved = alg_bytes / mean_launch_s / 1e9
     peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic(N, stages)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -623,7 +660,8 @@ def main():
             "plan": main_r["info"],
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(N, stages),
+                     "frac": achieved / peak, "traffic": traffic,
+                     "frac_dram": (traffic / mean_launch_s / 1e9 / peak) if traffic else None,
                      "peak_source": peak_kind,
                      "kernel": "sto_persistent_kernel",
                      "algorithmic_bytes_per_launch": alg_bytes,
@@ -667,6 +705,7 @@ def main():
         line["group"] = group
     if fp64 is not None:
         line["fp64"] = fp64
+    line["summary"] = summary(line, peak)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
