@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--sweep-r", type=int, default=512)
     ap.add_argument("--sweep-t", type=int, default=2, help="input samples per timed sweep call")
     ap.add_argument("--sweep-plan", default="",
-                    help="tile_n,slots[,groups[,staged]] of the sweep kernel (default: autotuned)")
+                    help="tile_n,slots[,groups[,staged[,threads]]] of the sweep kernel (default: autotuned)")
     ap.add_argument("--no-group", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
     ap.add_argument("--group-lanes", type=int, default=0, help="lanes of the group launch (0 = auto)")
@@ -434,6 +435,67 @@ def time_group(args, seed, torch, sto, dev, hbm_peak):
             "note": "one cooperative launch; members on different lanes run side by side"}
 
 
+def time_fused(args, seed, torch, sto, dev):
+    """The whole parameter sweep of the configuration in ONE persistent launch
+    per call (sto_run_sweep_group): the 512 shared-W reservoirs (tensor-core
+    product) on the SMs the 64 own-W reservoirs' lanes leave free.  The SM
+    split is a choice of the caller: a few are timed, the fastest reported."""
+    N, R, T = args.sweep_n, args.sweep_r, 1
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    W, w_in, _, u = workload(N, 4, seed)
+    rng = np.random.default_rng([seed, 7])
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=args.substeps)
+    stream = torch.cuda.current_stream()
+    sw = sto.Sweep(torch.from_numpy(W).to(dev), torch.from_numpy(w_in).to(dev), P, currents=cur, gains=gain,
+                   stream=stream)
+    grng = np.random.default_rng([seed, 11])
+    Ns = grng.integers(100, 4001, args.group_r)
+    res = []
+    for i, Ni in enumerate(Ns):
+        Wi, wi, mi, _ = workload(int(Ni), 1, seed + 5000 + i)
+        res.append(sto.Reservoir(torch.from_numpy(Wi).to(dev), torch.from_numpy(wi).to(dev), P,
+                                 m0=torch.from_numpy(mi).to(dev), stream=stream))
+    u_d = torch.from_numpy(u).to(dev)
+    splits = []
+    for sweep_sms in (20, 28, 36, 48):
+        try:
+            grp = sto.Group(res, lanes=0, ctas=sms - sweep_sms)
+        except sto.StoError as e:
+            splits.append({"sweep_sms": sweep_sms, "error": str(e)})
+            continue
+        info = grp.info()
+        sto.run_sweep_group(sw, grp, u_d[:T], T)  # warm-up (the sweep's autotuner on the first call)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for i in range(reps):
+            sto.run_sweep_group(sw, grp, u_d[T * (i + 1):T * (i + 2)], T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        grp.close()
+        splits.append({"sweep_sms": sweep_sms, "group_lanes": info["lanes"], "lane_width": info["lane_width"],
+                       "ms_per_call": ms, "us_per_stage": ms * 1e3 / (4 * args.substeps * T)})
+    plan = sw.plan()
+    sw.close()
+    for r in res:
+        r.close()
+    ok = [x for x in splits if "us_per_stage" in x]
+    best = min(ok, key=lambda x: x["us_per_stage"]) if ok else None
+    out = {"workload": f"{R} reservoirs sharing one N={N} Gaussian W (BF16), I~U[1,3] mA, g~U[0.5,2], plus "
+                       f"{args.group_r} reservoirs with their own Gaussian W, N~U[100,4000]; one input sample x "
+                       f"{args.substeps} RK4 steps per call, one cooperative launch per call",
+           "launches_per_call": 1, "splits": splits, "sweep_plan": plan}
+    if best:
+        out.update({"us_per_stage": best["us_per_stage"], "ms_per_call": best["ms_per_call"],
+                    "value": (R * N + float(np.sum(Ns))) * args.substeps * T / (best["ms_per_call"] / 1e3),
+                    "unit": "node-updates/s", "best_split": best})
+    return out
+
+
 def time_fp64(args, seed, torch, sto, dev, hbm_peak):
     """The paper's own benchmark in its precision (Sec. 3.3, Table 1): FP64
     coupling, u = 0, Eq. (initial) for every oscillator, W of the paper's
@@ -565,6 +627,10 @@ def summary(line, hbm_peak):
     grp = line.get("group")
     if grp:
         out.update({"group_us_per_stage": grp["us_per_stage"], "group_frac_hbm": grp["frac_of_hbm"]})
+    fu = line.get("sweep_and_group_one_launch")
+    if fu and "us_per_stage" in fu:
+        out.update({"sweep_and_group_one_launch_us_per_stage": fu["us_per_stage"],
+                    "sweep_and_group_separate_us_per_stage": fu.get("separate_launches_us_per_stage")})
     fp = line.get("fp64")
     if fp:
         for c in fp["cases"]:
@@ -607,6 +673,9 @@ def main():
     group = None
     if not args.no_group:
         group = time_group(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
+    fused = None
+    if not args.no_fused:
+        fused = time_fused(args, replica_seed(rank), torch, sto, dev)
     fp64 = None
     if not args.no_fp64:
         fp64 = time_fp64(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
@@ -703,6 +772,10 @@ def main():
         line["sweep"] = sweep
     if group is not None:
         line["group"] = group
+    if fused is not None:
+        if sweep is not None and group is not None:
+            fused["separate_launches_us_per_stage"] = sweep["us_per_stage"] + group["us_per_stage"]
+        line["sweep_and_group_one_launch"] = fused
     if fp64 is not None:
         line["fp64"] = fp64
     line["summary"] = summary(line, peak)

@@ -302,6 +302,13 @@ STO_API int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, st
  *         since creation), STO_ENOMEM, STO_ETIMEOUT, STO_ECUDA. */
 STO_API int sto_group_run(sto_group* g, const float* u, int64_t T, float* const* states_out);
 
+/* sto_group_create for a group that shares the GPU with a sweep in one
+ * launch (sto_run_sweep_group): its lanes occupy ctas CTAs (0 = one per SM,
+ * as sto_group_create), the other SMs are left to the sweep.  lanes = 0
+ * picks the lane count as sto_group_create does for that many CTAs.
+ * Errors: as sto_group_create; STO_EINVAL for ctas outside 0 .. #SMs. */
+STO_API int sto_group_create_ex(sto_handle* const* hs, int32_t n, int32_t lanes, int32_t ctas, sto_group** out);
+
 /* The lane count, the CTAs per lane, and (lane_of, n entries, or NULL) the
  * lane each member runs on.  Errors: STO_EINVAL. */
 STO_API int sto_group_get_info(const sto_group* g, int32_t* lanes, int32_t* lane_width, int32_t* lane_of);
@@ -362,6 +369,25 @@ STO_API int sto_batch_create(int64_t N, int32_t R, const sto_params* params,
  * Errors: STO_EINVAL, STO_ENOMEM, STO_ENOTSUP, STO_ETIMEOUT, STO_ECUDA. */
 STO_API int sto_run_batched(sto_batch* b, const float* u, int64_t T, float* states_out);
 
+/* A whole parameter sweep (Sec. 1 and Sec. 2: exploring the parameter
+ * space is the time-consuming part) in ONE persistent cooperative launch,
+ * captured as a CUDA graph: the shared-W reservoirs of b on the SMs that the
+ * own-W group g leaves free (#SMs - its lanes x lane width CTAs, created with
+ * sto_group_create_ex), g's lanes on the others, all over the same input
+ * series u (T x n_in, host or device; b and every member of g must have the
+ * same n_in, and the same device).  The sweep runs its current tile width,
+ * ring depth and group count with 512 threads per CTA (autotuned first if it
+ * has no plan), on as many of its SMs as balance its tiles; its plan for
+ * sto_run_batched is left as it was.  Each part gives the same bits as its
+ * own call (sto_run_batched, sto_group_run).
+ *   sweep_states_out  T x R x N float32 (host or device) or NULL.
+ *   group_states_out  NULL, or n pointers (T x N_i, host or device, or NULL).
+ * Errors: STO_EINVAL, STO_ENOTSUP (no SM left for the sweep, a member
+ *         re-planned since the group was made, shared memory), STO_ENOMEM,
+ *         STO_ETIMEOUT, STO_ECUDA. */
+STO_API int sto_run_sweep_group(sto_batch* b, sto_group* g, const float* u, int64_t T, float* sweep_states_out,
+                                float* const* group_states_out);
+
 /* Launch plan of the sweep kernel. */
 typedef struct {
   int32_t tile_n;              /* reservoirs per tile (BN): MMA N = 2 BN (hi and lo terms), multiple of 16 */
@@ -372,19 +398,22 @@ typedef struct {
   int32_t tuned;               /* 1: chosen by timing candidates; 0: set by the caller or none yet */
   int32_t candidates;          /* candidates the autotuner timed */
   float tuned_us_per_stage;    /* the winner's time per stage in the tuning run */
-  int32_t staged;              /* 1: the epilogue copies the next pair's state to shared memory ahead */
+  int32_t staged;              /* 1: the update loads the next pair's state into registers while it
+                                  computes the current pair */
   int32_t groups;              /* reservoir groups with their own grid barriers (1 or 2): with 2, one
                                   group's tensor-core product overlaps the other's update */
-  int32_t reserved[2];
+  int32_t threads;             /* threads per CTA: 512 (12 update warps of 128 registers) or 1024
+                                  (28 update warps of 64 registers) */
+  int32_t reserved;
 } sto_batch_plan;
 
 /* Set the plan: tile_n (multiple of 8 in [16, 128]) and slots (2 to 9 ring
  * slots of two 64-wide K slices each: 2 (16 KB + 256 tile_n B) of shared
- * memory per slot; three copy warps, warp p owning the slots s = p mod 3;
- * the state staging buffer is used when it fits beside the ring), with one
- * reservoir group, or (0, 0) to time every candidate (tile_n in {16, 32, 40,
- * 48, 64, ..., 128} up to R, slots in {2, 3, 4, 5}, staging on and off, 1 and
- * 2 groups) on two RK4 steps of zero
+ * memory per slot; three copy warps, warp p owning the slots s = p mod 3),
+ * with one reservoir group and 512 threads per CTA, or (0, 0) to time every
+ * candidate (tile_n in {16, 32, 40, 48, 64, ..., 128} up to R, slots in
+ * {2, 3, 4, 5}, the next pair's state loaded ahead or not, 1 and 2 groups,
+ * 512 and 1024 threads) on two RK4 steps of zero
  * input from the batch's state (restored afterwards) and keep the fastest.
  * Tuned plans are cached per (device, N, R) for the life of the process.
  * The stage state is kept.
@@ -400,14 +429,20 @@ STO_API int sto_batch_set_plan(sto_batch* b, int32_t tile_n, int32_t slots);
  * STO_EINVAL for groups outside 1..2. */
 STO_API int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups);
 
-/* sto_batch_set_plan_ex with the staging mode: staged = 1 copies each
- * pair's state into shared memory ahead of its update (STO_ENOTSUP when it
- * does not fit beside the ring), 0 reads it from global memory in the
- * update, -1 stages when it fits (as sto_batch_set_plan_ex).  Lets a caller
- * (or a profiler run) fix exactly the plan the autotuner chose.  Errors: as
- * sto_batch_set_plan_ex; STO_EINVAL for staged outside -1..1. */
+/* sto_batch_set_plan_ex with the staging mode: staged = 1 loads the next
+ * pair's state into registers while the current pair is computed (and the
+ * first pair's while the tile's product runs), 0 loads each pair's state
+ * when it is needed, -1 chooses (1 with 512 threads).  512 threads per CTA.
+ * Errors: as sto_batch_set_plan_ex; STO_EINVAL for staged outside -1..1. */
 STO_API int sto_batch_set_plan_staged(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups,
                                       int32_t staged);
+
+/* sto_batch_set_plan_staged with the threads per CTA: 512 (12 update warps,
+ * 128 registers each) or 1024 (28 update warps, 64 registers each).  Lets a
+ * caller (or a profiler run) fix exactly the plan the autotuner chose.
+ * Errors: as sto_batch_set_plan_staged; STO_EINVAL for other thread counts. */
+STO_API int sto_batch_set_plan_threads(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups,
+                                       int32_t staged, int32_t threads);
 
 /* The current plan (all zero before the first run or set_plan). */
 STO_API int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out);

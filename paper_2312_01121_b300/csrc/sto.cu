@@ -755,12 +755,16 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
 // in the same order under any plan, except that a plan holding W on chip
 // with at most two rows per warp keeps four partial sums per row: the new
 // plan can change the last bits of the coupling sums.
-int replan_handle(sto_handle* h, int G) {
-  if (h->plan.G == G) return STO_OK;
+// Re-plan for G CTAs with at most smem_optin - reserve bytes of dynamic
+// shared memory per CTA (reserve: static shared memory of the kernel that
+// will run the plan beside its own).
+int replan_handle(sto_handle* h, int G, size_t reserve = 0) {
   int smem_optin = 0;
   STO_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  const size_t smem_max = static_cast<size_t>(smem_optin) - reserve;
+  if (h->plan.G == G && h->plan.smem <= smem_max) return STO_OK;
   Plan p;
-  int rc = make_plan(h->N, G, h->sm_count, static_cast<size_t>(smem_optin), &p, h->wmode);
+  int rc = make_plan(h->N, G, h->sm_count, smem_max, &p, h->wmode);
   if (rc) return rc;
   if (p.P != h->plan.P) return STO_ENOTSUP;
   const size_t elems = static_cast<size_t>(h->N) * p.P * sto::kPanelCols;
@@ -1164,16 +1168,21 @@ int sto_run_group(sto_handle* const* hs, int32_t n, const float* u, int64_t T,
 }
 
 int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group** out) {
+  return sto_group_create_ex(hs, n, lanes, 0, out);
+}
+
+int sto_group_create_ex(sto_handle* const* hs, int32_t n, int32_t lanes, int32_t ctas, sto_group** out) {
   if (!out) return STO_EINVAL;
   *out = nullptr;
-  if (!hs || n < 1 || lanes < 0) return STO_EINVAL;
+  if (!hs || n < 1 || lanes < 0 || ctas < 0) return STO_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (!hs[i] || hs[i]->params.n_in != hs[0]->params.n_in || hs[i]->device != hs[0]->device) return STO_EINVAL;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return STO_EINVAL;
     if (hs[i]->wmode != sto::kWf32) return STO_ENOTSUP;  // the group kernel runs the FP32 coupling
   }
-  const int sms = hs[0]->sm_count;
+  if (ctas > hs[0]->sm_count) return STO_EINVAL;
+  const int sms = ctas > 0 ? ctas : hs[0]->sm_count;  // the CTAs the group's lanes share
   int64_t n_min = hs[0]->N, n_max = hs[0]->N;
   for (int i = 0; i < n; ++i) {
     n_min = hs[i]->N < n_min ? hs[i]->N : n_min;
@@ -1197,8 +1206,19 @@ int sto_group_create(sto_handle* const* hs, int32_t n, int32_t lanes, sto_group*
   g->n = n;
   g->lanes = L;
   g->width = sms / L;
+  // a group that shares its launch with a sweep (ctas > 0) runs inside
+  // sweep_group_kernel, whose static shared memory its plans leave room for
+  size_t reserve = 0;
+  if (ctas > 0) {
+    cudaFuncAttributes fa{};
+    if (const cudaError_t e = cudaFuncGetAttributes(&fa, sto::sweep_group_kernel)) {
+      free_group(g);
+      return cuda_fail(e);
+    }
+    reserve = fa.sharedSizeBytes;
+  }
   for (int i = 0; i < n; ++i) {
-    const int rc = replan_handle(hs[i], g->width);
+    const int rc = replan_handle(hs[i], g->width, reserve);
     if (rc) {
       free_group(g);
       return rc;
@@ -1485,8 +1505,12 @@ int sto_run_noalloc(int64_t N, const sto_params* params, const float* W, const f
 struct SweepPlan {
   int bn = 0, slots = 0, G = 0, tiles_m = 0, tiles_n = 0, acc_cols = 0, staged = 0;
   int groups = 1, tn_split = 0;  // reservoir groups with their own barriers (see sweep.cuh)
+  int epq = 3;                   // epilogue warps per TMEM lane quarter: 3 (512 threads) or 7 (1024)
   size_t smem = 0;
 };
+
+// Threads per CTA of the sweep kernel with epq epilogue warps per quarter.
+int sweep_threads(int epq) { return epq == 7 ? sto::sp_threads<7>() : sto::sp_threads<3>(); }
 
 }  // namespace
 
@@ -1544,8 +1568,10 @@ void free_batch(sto_batch* b) {
 // of the hi/lo stack is a multiple of 16, a tcgen05 M = 128 shape), shared
 // memory within the device limit, every CTA resident (one per SM), and with
 // two groups at least two tile columns.
-bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, SweepPlan* out) {
-  if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < 2 || slots > sto::kSpMaxSlots || groups < 1 || groups > 2)
+bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, int epq, SweepPlan* out,
+                int max_ctas = 0) {
+  if (bn < 16 || bn > 128 || bn % 8 != 0 || slots < 2 || slots > sto::kSpMaxSlots || groups < 1 || groups > 2 ||
+      (epq != 3 && epq != 7) || (staged && epq != 3))  // 64 registers leave no room to load ahead
     return false;
   SweepPlan p;
   p.bn = bn;
@@ -1557,24 +1583,30 @@ bool sweep_plan(const sto_batch* b, int bn, int slots, int staged, int groups, S
   p.tn_split = groups == 2 ? (p.tiles_n + 1) / 2 : p.tiles_n;
   p.acc_cols = 2 * bn <= 32 ? 32 : (2 * bn <= 64 ? 64 : (2 * bn <= 128 ? 128 : 256));  // [hi | lo] columns
   p.staged = staged ? 1 : 0;
+  p.epq = epq;
   p.smem = static_cast<size_t>(slots) * sto::kSlotK * (sto::kSwSliceA + 2u * bn * sto::kSwK * 2u) +
-           (staged ? sto::kSpStageAll : 0) + sto::kSpAlignSlack;
-  const int room = raise_dyn_smem_cap(sto::sweep_persistent_kernel);
+           sto::kSpAlignSlack;
+  const int room = epq == 7 ? raise_dyn_smem_cap(sto::sweep_persistent_kernel<7>)
+                            : raise_dyn_smem_cap(sto::sweep_persistent_kernel<3>);
   if (room < 0 || p.smem > static_cast<size_t>(room)) return false;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sto::sweep_persistent_kernel, sto::kSpThreads,
-                                                    p.smem) != cudaSuccess ||
-      per_sm < 1) {
+  const cudaError_t occ =
+      epq == 7 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sto::sweep_persistent_kernel<7>,
+                                                               sweep_threads(7), p.smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sto::sweep_persistent_kernel<3>,
+                                                               sweep_threads(3), p.smem);
+  if (occ != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return false;
   }
   // balanced grid: the fewest CTAs that keep the most loaded one at the
   // minimum number of tiles (of the larger group)
   const long long n_tiles = static_cast<long long>(p.tiles_m) * p.tn_split;
-  const long long slots_avail = static_cast<long long>(sms) * 1;  // one CTA per SM (928 threads)
+  // one CTA per SM, on at most max_ctas SMs when given
+  const long long slots_avail = static_cast<long long>(max_ctas > 0 && max_ctas < sms ? max_ctas : sms);
   const long long per = (n_tiles + slots_avail - 1) / slots_avail;
   p.G = static_cast<int>((n_tiles + per - 1) / per);
   *out = p;
@@ -1601,19 +1633,20 @@ int sweep_apply_plan(sto_batch* b, const SweepPlan& p) {
   const size_t RN = static_cast<size_t>(b->R) * b->N;
   STO_CUDA(cudaMemsetAsync(b->X[0], 0, need * 2, s));
   STO_CUDA(cudaMemsetAsync(b->X[1], 0, need * 2, s));
+  // between calls the next stage is stage 0, evaluated at m_n (the stage
+  // state array is not rewritten by stage 3)
   sto::sweep_publish_kernel<<<static_cast<unsigned>((RN + 255) / 256), 256, 0, s>>>(
-      b->st + 3 * RN, b->X[0], static_cast<int>(b->N), b->R, b->Kpad, p.bn);
+      b->st, b->X[0], static_cast<int>(b->N), b->R, b->Kpad, p.bn);
   STO_CUDA(cudaGetLastError());
   b->plan = p;
   b->planned = true;
   return STO_OK;
 }
 
-// Enqueue one persistent launch over T input samples on the sweep's stream.
-int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float* d_states) {
+// Kernel arguments of a sweep launch over T input samples with plan p.
+sto::SweepArgs sweep_args(const sto_batch* b, const SweepPlan& p, const float* d_u, int64_t T, int substeps,
+                          float* d_states) {
   const sto_params& P = b->params;
-  const SweepPlan& p = b->plan;
-  cudaStream_t s = b->own;
   sto::SweepArgs a{};
   const size_t RN = static_cast<size_t>(b->R) * b->N;
   a.Wb = b->Wb;
@@ -1646,10 +1679,18 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
   a.staged = p.staged;
   a.timeout_ns = static_cast<unsigned long long>(kDefaultTimeoutMs) * 1000000ULL;
   set_constants(P, &a.c);
+  return a;
+}
+
+// Enqueue one persistent launch over T input samples on the sweep's stream.
+int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float* d_states) {
+  const SweepPlan& p = b->plan;
+  cudaStream_t s = b->own;
+  const sto::SweepArgs a = sweep_args(b, p, d_u, T, substeps, d_states);
   STO_CUDA(cudaMemsetAsync(b->gbar, 0, 16, s));  // one counter per group
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.G);
-  cfg.blockDim = dim3(sto::kSpThreads);
+  cfg.blockDim = dim3(sweep_threads(p.epq));
   cfg.dynamicSmemBytes = p.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1657,7 +1698,10 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  STO_CUDA(cudaLaunchKernelEx(&cfg, sto::sweep_persistent_kernel, a));
+  if (p.epq == 7)
+    STO_CUDA(cudaLaunchKernelEx(&cfg, sto::sweep_persistent_kernel<7>, a));
+  else
+    STO_CUDA(cudaLaunchKernelEx(&cfg, sto::sweep_persistent_kernel<3>, a));
   return STO_OK;
 }
 
@@ -1665,6 +1709,7 @@ int sweep_enqueue(sto_batch* b, const float* d_u, int64_t T, int substeps, float
 constexpr int kTuneBn[] = {16, 32, 40, 48, 64, 80, 96, 112, 128};
 constexpr int kTuneSlots[] = {2, 3, 4, 5};
 constexpr int kTuneGroups[] = {1, 2};
+constexpr int kTuneEpq[] = {3, 7};
 
 struct TuneKey {
   int dev;
@@ -1676,9 +1721,9 @@ struct TuneKey {
 };
 
 // Process-wide cache of tuned plans (bn, slots * 2 + staged, groups,
-// measured us per stage).
-std::map<TuneKey, std::array<float, 4>>& tune_cache() {
-  static std::map<TuneKey, std::array<float, 4>> m;
+// measured us per stage, epilogue warps per quarter).
+std::map<TuneKey, std::array<float, 5>>& tune_cache() {
+  static std::map<TuneKey, std::array<float, 5>> m;
   return m;
 }
 std::mutex& tune_mutex() {
@@ -1699,7 +1744,8 @@ int sweep_autotune(sto_batch* b) {
     if (it != tune_cache().end()) {
       SweepPlan p;
       const int code = static_cast<int>(it->second[1]);
-      if (sweep_plan(b, static_cast<int>(it->second[0]), code / 2, code % 2, static_cast<int>(it->second[2]), &p)) {
+      if (sweep_plan(b, static_cast<int>(it->second[0]), code / 2, code % 2, static_cast<int>(it->second[2]),
+                     static_cast<int>(it->second[4]), &p)) {
         const int rc = sweep_apply_plan(b, p);
         if (rc) return rc;
         b->tuned = 1;
@@ -1739,10 +1785,11 @@ int sweep_autotune(sto_batch* b) {
   for (int bn : kTuneBn) {
     if (bn > ((b->R + 15) / 16) * 16) break;  // tiles wider than R only add padding
     constexpr int kSlotsN = static_cast<int>(sizeof(kTuneSlots) / sizeof(kTuneSlots[0]));
-    for (int cand = 0; cand < 4 * kSlotsN; ++cand) {
-      const int slots = kTuneSlots[(cand / 2) % kSlotsN], staged = cand % 2, groups = kTuneGroups[cand / (2 * kSlotsN)];
+    for (int cand = 0; cand < 8 * kSlotsN; ++cand) {
+      const int slots = kTuneSlots[(cand / 2) % kSlotsN], staged = cand % 2,
+                groups = kTuneGroups[(cand / (2 * kSlotsN)) % 2], epq = kTuneEpq[cand / (4 * kSlotsN)];
       SweepPlan p;
-      if (!sweep_plan(b, bn, slots, staged, groups, &p)) continue;
+      if (!sweep_plan(b, bn, slots, staged, groups, epq, &p)) continue;
       if ((rc = sweep_apply_plan(b, p)) != STO_OK) break;
       float ms = 0.f;
       for (int rep = 0; rep < 3 && rc == STO_OK; ++rep) {
@@ -1795,7 +1842,7 @@ int sweep_autotune(sto_batch* b) {
   b->tuned_us = best;
   std::lock_guard<std::mutex> lk(tune_mutex());
   tune_cache()[key] = {static_cast<float>(best_p.bn), static_cast<float>(best_p.slots * 2 + best_p.staged),
-                       static_cast<float>(best_p.groups), best};
+                       static_cast<float>(best_p.groups), best, static_cast<float>(best_p.epq)};
   return STO_OK;
 }
 
@@ -1935,15 +1982,20 @@ int sto_batch_set_plan_ex(sto_batch* b, int32_t tile_n, int32_t slots, int32_t g
 }
 
 int sto_batch_set_plan_staged(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups, int32_t staged) {
+  return sto_batch_set_plan_threads(b, tile_n, slots, groups, staged, 512);
+}
+
+int sto_batch_set_plan_threads(sto_batch* b, int32_t tile_n, int32_t slots, int32_t groups, int32_t staged,
+                               int32_t threads) {
   if (!b) return STO_EINVAL;
   if (groups < 1 || groups > 2 || staged < -1 || staged > 1) return STO_EINVAL;
+  if (threads != sweep_threads(3) && threads != sweep_threads(7)) return STO_EINVAL;
   cudaStreamSynchronize(b->stream);
   if (tile_n == 0 && slots == 0) return sweep_autotune(b);
   SweepPlan p;
-  // staged = -1: stage the epilogue's state through shared memory when it fits beside the ring
-  const bool found = staged == -1 ? (sweep_plan(b, tile_n, slots, 1, groups, &p) ||
-                                     sweep_plan(b, tile_n, slots, 0, groups, &p))
-                                  : sweep_plan(b, tile_n, slots, staged, groups, &p);
+  const int epq = threads == sweep_threads(7) ? 7 : 3;
+  // staged = -1: hold the next pair's state in registers where the threads have room (512 threads)
+  const bool found = sweep_plan(b, tile_n, slots, staged == -1 ? (epq == 3 ? 1 : 0) : staged, groups, epq, &p);
   if (!found) return STO_ENOTSUP;
   int rc = sweep_apply_plan(b, p);
   if (rc) return rc;
@@ -1967,6 +2019,7 @@ int sto_batch_get_plan(const sto_batch* b, sto_batch_plan* out) {
   out->tuned_us_per_stage = b->tuned_us;
   out->staged = b->plan.staged;
   out->groups = b->plan.groups;
+  out->threads = sweep_threads(b->plan.epq);
   return STO_OK;
 }
 
@@ -2050,6 +2103,150 @@ void sto_batch_destroy(sto_batch* b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- sweep and group in one launch
+
+extern "C" int sto_run_sweep_group(sto_batch* b, sto_group* g, const float* u, int64_t T, float* sweep_states_out,
+                                   float* const* group_states_out) {
+  if (!b || !g || T < 0) return STO_EINVAL;
+  if (T == 0) return STO_OK;
+  if (!u) return STO_EINVAL;
+  const int n = g->n;
+  sto_handle* h0 = g->hs[0];
+  const sto_params& P = b->params;
+  if (h0->params.n_in != P.n_in) return STO_EINVAL;
+  int dev = 0;
+  STO_CUDA(cudaGetDevice(&dev));
+  if (dev != h0->device) return STO_EINVAL;
+  if (T > (1LL << 31) - 1 || 4ULL * static_cast<uint64_t>(P.substeps) * static_cast<uint64_t>(T) > 0x40000000ULL)
+    return STO_ENOTSUP;
+  for (int i = 0; i < n; ++i) {
+    sto_handle* h = g->hs[i];
+    if (!h->rk_classic || h->wmode != sto::kWf32 || h->plan.G != g->width || h->plan.regw) return STO_ENOTSUP;
+    if (4ULL * static_cast<uint64_t>(h->params.substeps) * static_cast<uint64_t>(T) > 0x40000000ULL)
+      return STO_ENOTSUP;
+  }
+  const int ctas_g = g->lanes * g->width;
+  const int sweep_ctas = h0->sm_count - ctas_g;  // the SMs the group leaves to the sweep
+  if (sweep_ctas < 1) return STO_ENOTSUP;
+  cudaStream_t s = b->stream;
+  int rc;
+  if (!b->planned) {
+    cudaStreamSynchronize(s);
+    if ((rc = sweep_autotune(b))) return rc;
+  }
+  // the batch's tile width on the sweep's SMs, 512 threads; the X layout
+  // depends only on the tile width, so the batch's buffers and plan stay
+  SweepPlan pf;
+  if (!sweep_plan(b, b->plan.bn, b->plan.slots, 1, b->plan.groups, 3, &pf, sweep_ctas) &&
+      !sweep_plan(b, b->plan.bn, b->plan.slots, 1, 1, 3, &pf, sweep_ctas))
+    return STO_ENOTSUP;
+  const size_t smem = pf.smem > g->smem ? pf.smem : g->smem;
+  const int room = raise_dyn_smem_cap(sto::sweep_group_kernel);
+  if (room < 0 || smem > static_cast<size_t>(room)) return STO_ENOTSUP;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sto::sweep_group_kernel, sto::kThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return STO_ENOTSUP;
+  }
+  // inputs and outputs on the device
+  const size_t n_u = static_cast<size_t>(T) * P.n_in;
+  if ((rc = grow(&b->d_u, &b->d_u_cap, n_u))) return rc;
+  STO_CUDA(cudaMemcpyAsync(b->d_u, u, n_u * 4, cudaMemcpyDefault, s));
+  const size_t n_sw = static_cast<size_t>(T) * b->R * b->N;
+  float* d_sw = sweep_states_out;
+  const bool host_sw = sweep_states_out && !is_device_ptr(sweep_states_out);
+  if (host_sw) {
+    if ((rc = grow(&b->d_states, &b->d_states_cap, n_sw))) return rc;
+    d_sw = b->d_states;
+  }
+  std::vector<float*> d_gs(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    float* so = group_states_out ? group_states_out[i] : nullptr;
+    d_gs[i] = so;
+    if (so && !is_device_ptr(so)) {
+      if ((rc = grow(&g->hs[i]->d_states, &g->hs[i]->d_states_cap, static_cast<size_t>(T) * g->hs[i]->N)))
+        return rc;
+      d_gs[i] = g->hs[i]->d_states;
+    }
+  }
+  STO_CUDA(cudaStreamSynchronize(h0->stream));  // the pinned job records are free to rewrite
+  for (int i = 0; i < n; ++i) {
+    sto::KArgs a = base_args(g->hs[i], b->d_u, T);
+    a.states_out = d_gs[i];
+    a.err = g->d_errs + 4 * i;
+    g->h_jobs[i] = a;
+  }
+  // the launch follows the caller's and every member's earlier work
+  STO_CUDA(cudaEventRecord(b->ev, s));
+  STO_CUDA(cudaStreamWaitEvent(b->own, b->ev, 0));
+  for (int i = 0; i < n; ++i) {
+    STO_CUDA(cudaEventRecord(b->ev, g->hs[i]->stream));
+    STO_CUDA(cudaStreamWaitEvent(b->own, b->ev, 0));
+  }
+  sto::SweepGroupArgs f{};
+  f.sw = sweep_args(b, pf, b->d_u, T, P.substeps, d_sw);
+  f.grp.jobs = g->d_jobs;
+  f.grp.lane_begin = g->d_tab;
+  f.grp.order = g->d_tab + g->lane_begin.size();
+  f.grp.rpw = g->d_tab + g->lane_begin.size() + g->order.size();
+  f.grp.n_lanes = g->lanes;
+  f.grp.lane_width = g->width;
+  f.sweep_ctas = pf.G;
+  // the call (counters and error words reset, job records, one persistent
+  // launch) as a CUDA graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  STO_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(b->gbar, 0, 16, b->own);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 16, b->own);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_errs, 0, sizeof(int) * 4 * n, b->own);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->d_jobs, g->h_jobs, sizeof(sto::KArgs) * n, cudaMemcpyHostToDevice, b->own);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pf.G + ctas_g);
+    cfg.blockDim = dim3(sto::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->own;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA of both roles resident
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, sto::sweep_group_kernel, f);
+  }
+  const cudaError_t ce = cudaStreamEndCapture(b->own, &graph);
+  if (e != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e != cudaSuccess ? e : ce);
+  }
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->own);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->own);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->h_errs, g->d_errs, sizeof(int) * 4 * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && host_sw) e = cudaMemcpyAsync(sweep_states_out, d_sw, n_sw * 4, cudaMemcpyDeviceToHost, s);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    float* so = group_states_out ? group_states_out[i] : nullptr;
+    if (so && so != d_gs[i])
+      e = cudaMemcpyAsync(so, d_gs[i], static_cast<size_t>(T) * g->hs[i]->N * 4, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  rc = STO_OK;
+  if (b->h_err[0] != 0) rc = b->h_err[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  for (int i = 0; i < n; ++i) {
+    g->hs[i]->inject_cta = -1;
+    if (g->h_errs[4 * i] != 0 && rc == STO_OK) rc = g->h_errs[4 * i] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  }
+  return rc;
+}
 
 // ---------------------------------------------------------------- readout
 //

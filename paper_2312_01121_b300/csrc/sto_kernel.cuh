@@ -1398,10 +1398,11 @@ struct GroupArgs {
   int n_lanes, lane_width;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) sto_group_kernel(const __grid_constant__ GroupArgs g) {
-  const int lane = static_cast<int>(blockIdx.x) / g.lane_width;
+// CTA `cta` of the group's n_lanes * lane_width CTAs.
+__device__ __forceinline__ void group_cta(const GroupArgs& g, const int cta) {
+  const int lane = cta / g.lane_width;
   if (lane >= g.n_lanes) return;
-  const int c = static_cast<int>(blockIdx.x) - lane * g.lane_width;
+  const int c = cta - lane * g.lane_width;
   for (int i = g.lane_begin[lane]; i < g.lane_begin[lane + 1]; ++i) {
     const int j = g.order[i];
     const KArgs& a = g.jobs[j];
@@ -1415,6 +1416,10 @@ __global__ void __launch_bounds__(kThreads, 1) sto_group_kernel(const __grid_con
     // copies) before the next one re-initialises shared memory
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) sto_group_kernel(const __grid_constant__ GroupArgs g) {
+  group_cta(g, static_cast<int>(blockIdx.x));
 }
 
 // Re-tile W from the layout of a plan with G_old CTAs to one with G_new

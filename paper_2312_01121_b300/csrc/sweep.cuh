@@ -62,14 +62,19 @@ constexpr int kSwSliceA = kSwM * kSwK * 2;             // 16 KB of W per slice
 // MMA thread's fixed cost per slot is about that of 4 MMAs); Kpad is a
 // multiple of kSlotK * kSwK
 constexpr int kSlotK = 2;
-constexpr int kSpEpiPerQuarter = 7;                    // epilogue warps per TMEM lane quarter
-constexpr int kSpEpiWarps = 4 * kSpEpiPerQuarter;      // 28
 // Three warps issue the copies, warp p owning the ring slots s = p (mod 3);
 // the ring holds 2 to 9 slots (with 2 the third copy warp idles).
 constexpr int kSpProducers = 3;
 constexpr int kSpEpiFirst = 1 + kSpProducers;          // warp 0 multiplies, 1..3 copy
-constexpr int kSpThreads = 32 * (kSpEpiFirst + kSpEpiWarps);  // 1024
 constexpr int kSpMaxSlots = 9;
+// Epilogue warps per TMEM lane quarter (EPQ, a template parameter of the
+// kernel): 7 (1024 threads of 64 registers) or 3 (512 threads of 128
+// registers, room to hold the next pair's state while the current one is
+// computed, and the block shape of the single-reservoir stepper).
+template <int EPQ>
+constexpr int sp_threads() {
+  return 32 * (kSpEpiFirst + 4 * EPQ);
+}
 
 struct SweepArgs {
   const __nv_bfloat16* Wb;   // Wt tiles
@@ -88,7 +93,7 @@ struct SweepArgs {
   int N, R, Kpad, n_in, comp, S, T;
   int bn, slots, tiles_m, tiles_n, acc_cols;  // plan: tile width, ring depth, tiles, TMEM columns per accumulator
   int groups, tn_split;      // reservoir groups (1 or 2); group 0 = tile columns [0, tn_split)
-  int staged;                // 1: the next pair's state is copied to shared memory ahead (cp.async)
+  int staged;                // 1: the next pair's state is loaded into registers ahead
   unsigned long long timeout_ns;
   KArgs c;                   // shared constants (gdt, alpha, happl, hkp, lambda, p, acp, sixth)
 };
@@ -204,17 +209,6 @@ __device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsig
   }
 }
 
-// Asynchronous 8-byte global -> shared copy (no register staging).
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Shared-memory staging of one pair's state per epilogue lane: mn, ms, ks
-// (3 float2 each).
-constexpr int kSpStageBytes = 9 * 8 * 32;                  // per epilogue warp
-constexpr int kSpStageAll = kSpStageBytes * kSpEpiWarps;   // 64.5 KB
 constexpr int kSpAlignSlack = 1024;                        // room to align the ring
 
 __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
@@ -260,97 +254,91 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int q, int idx, i
 }
 
 // The epilogue of one tile for one epilogue warp: the pairs (reservoir
-// tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + 7, ...
-// The state of the next column's pair is copied into shared memory (stg)
-// while the current one is computed when STAGED.  tacc addresses this
-// warp's TMEM lanes of the accumulator; xk is the X offset of (jc = 0, k).
-// Returns false when the accumulator never filled (timeout or abort).
-template <int ST, bool STAGED>
-__device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, float2* stg, uint32_t tacc, int tn,
-                                                  unsigned k, bool row_ok, unsigned xk, unsigned kchunk,
-                                                  df drive, int t, bool sample, __nv_bfloat16* Xn,
-                                                  unsigned lo_off, int wi, int lane, uint64_t* acc_bar,
-                                                  uint32_t acc_parity, const volatile int* abort_flag) {
-  const unsigned R = static_cast<unsigned>(a.R), N = static_cast<unsigned>(a.N), RN = R * N;
-  constexpr unsigned kStep = kSpEpiPerQuarter;
-  const unsigned istep = kStep * N;
-  unsigned r = static_cast<unsigned>(tn * a.bn + wi), idx = r * N + k;
-  auto prefetch = [&](unsigned rr, unsigned ii) {
-    if (row_ok && rr < R) {
+// tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + EPQ,
+// ...  With PREF the state of the next column's pair is loaded into
+// registers while the current one is computed, and the first pair's before
+// the accumulator is waited for (the loads overlap the tile's MMAs).  tacc
+// addresses this warp's TMEM lanes of the accumulator; xk is the X offset of
+// (jc = 0, k).  Returns false when the accumulator never filled (timeout or
+// abort).
+// The state of one pair (mn; ms and ks when ST > 0) read from the [3][R][N]
+// arrays at element idx, or zeros for a pair outside the batch.
+struct PairState {
+  df m[3], s[3], k[3];
+};
+template <int ST>
+__device__ __forceinline__ PairState load_pair(const SweepArgs& a, unsigned RN, unsigned idx, bool ok) {
+  PairState p;
+  if (ok) {
 #pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        cp_async8(stg + (qq * 32 + lane), a.mn + (qq * RN + ii));
-        if constexpr (ST > 0) {
-          cp_async8(stg + ((3 + qq) * 32 + lane), a.ms + (qq * RN + ii));
-          cp_async8(stg + ((6 + qq) * 32 + lane), a.ksum + (qq * RN + ii));
-        }
+    for (int qq = 0; qq < 3; ++qq) {
+      const float2 x0 = a.mn[qq * RN + idx];
+      p.m[qq] = df{x0.x, x0.y};
+      if constexpr (ST > 0) {
+        const float2 x1 = a.ms[qq * RN + idx], x2 = a.ksum[qq * RN + idx];
+        p.s[qq] = df{x1.x, x1.y};
+        p.k[qq] = df{x2.x, x2.y};
       }
     }
-    cp_async_commit();
-  };
-  if constexpr (STAGED) prefetch(r, idx);  // overlaps the tile's MMAs
-  const bool landed = mbar_wait_bounded(acc_bar, acc_parity, a.timeout_ns, abort_flag);
-  if (!__all_sync(0xffffffffu, landed)) {
-    if constexpr (STAGED) cp_async_wait_all();
-    return false;
+  } else {
+    p = PairState{};
   }
+  return p;
+}
+
+template <int ST, bool PREF, int EPQ>
+__device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, uint32_t tacc, int tn, unsigned k,
+                                                  bool row_ok, unsigned xk, unsigned kchunk, df drive, int t,
+                                                  bool sample, __nv_bfloat16* Xn, unsigned lo_off, int wi,
+                                                  uint64_t* acc_bar, uint32_t acc_parity,
+                                                  const volatile int* abort_flag) {
+  const unsigned R = static_cast<unsigned>(a.R), N = static_cast<unsigned>(a.N), RN = R * N;
+  constexpr unsigned kStep = EPQ;
+  const unsigned istep = kStep * N;
+  unsigned r = static_cast<unsigned>(tn * a.bn + wi), idx = r * N + k;
+  PairState cur, nxt;
+  if constexpr (PREF) nxt = load_pair<ST>(a, RN, idx, row_ok && r < R);
+  const bool landed = mbar_wait_bounded(acc_bar, acc_parity, a.timeout_ns, abort_flag);
+  if (!__all_sync(0xffffffffu, landed)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   for (int jc = wi; jc < a.bn; jc += kStep, r += kStep, idx += istep) {
     uint32_t vh, vl;  // W X_hi and W X_lo of this pair
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(vh) : "r"(tacc + jc));
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(vl) : "r"(tacc + a.bn + jc));
+    const bool pair_ok = row_ok && r < R;
+    if constexpr (PREF) {
+      cur = nxt;
+      if (jc + static_cast<int>(kStep) < a.bn) nxt = load_pair<ST>(a, RN, idx + istep, row_ok && r + kStep < R);
+    } else {
+      cur = load_pair<ST>(a, RN, idx, pair_ok);
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const float hraw = __fadd_rn(__uint_as_float(vh), __uint_as_float(vl));
-    const bool pair_ok = row_ok && r < R;
-    df mn[3], ms[3], ks[3];
-    if constexpr (STAGED) {
-      cp_async_wait_all();
-#pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        const float2 x0 = stg[qq * 32 + lane];
-        mn[qq] = df{x0.x, x0.y};
-        if constexpr (ST > 0) {
-          const float2 x1 = stg[(3 + qq) * 32 + lane], x2 = stg[(6 + qq) * 32 + lane];
-          ms[qq] = df{x1.x, x1.y};
-          ks[qq] = df{x2.x, x2.y};
-        }
-      }
-      if (jc + static_cast<int>(kStep) < a.bn) prefetch(r + kStep, idx + istep);
-    } else if (pair_ok) {
-#pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        const float2 x0 = a.mn[qq * RN + idx];
-        mn[qq] = df{x0.x, x0.y};
-        if constexpr (ST > 0) {
-          const float2 x1 = a.ms[qq * RN + idx], x2 = a.ksum[qq * RN + idx];
-          ms[qq] = df{x1.x, x1.y};
-          ks[qq] = df{x2.x, x2.y};
-        }
-      }
-    }
     if (pair_ok) {
       const unsigned xo = xk + static_cast<unsigned>(jc) * 64u + ((kchunk ^ (static_cast<unsigned>(jc) & 7u)) << 3);
-      sweep_pair<ST>(a, r, idx, RN, hraw, t, sample, drive, mn, ms, ks, Xn, xo, lo_off);
+      sweep_pair<ST>(a, r, idx, RN, hraw, t, sample, drive, cur.m, cur.s, cur.k, Xn, xo, lo_off);
     }
   }
   return true;
 }
 
-// The whole sweep call: 4 S T stages of every group.  Warp 0 (one thread)
-// passes each unit's group barrier, releases the unit to the copy warps and
-// issues the MMAs; warps 1-3 (one thread each) fill their ring slots; warps
-// 4-31 run the epilogue.
-__global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
-  extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
+// The whole sweep call for CTA `cta` of the G CTAs that run it: 4 S T
+// stages of every group.  Warp 0 (one thread) passes each unit's group
+// barrier, releases the unit to the copy warps and issues the MMAs; warps
+// 1-3 (one thread each) fill their ring slots; the other 4 EPQ warps run the
+// epilogue.  smem_raw: the CTA's dynamic shared memory (the ring).
+template <int EPQ>
+__device__ __forceinline__ void sweep_cta(const SweepArgs& a, const int cta, const int G,
+                                          unsigned char* smem_raw) {
+  constexpr int kSpEpiWarps = 4 * EPQ;
   // the swizzle pattern repeats every 1024 B: the ring starts on such a boundary
-  unsigned char* sp_smem = sp_smem_raw + ((1024u - (smem_u32(sp_smem_raw) & 1023u)) & 1023u);
+  unsigned char* sp_smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t full[kSpMaxSlots], empty[kSpMaxSlots], acc_full[2], acc_empty[2];
   __shared__ uint64_t stage_done[2], drain;
   __shared__ unsigned long long s_go;  // units released to the copy warps
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = gridDim.x, cta = blockIdx.x;
   const int n_grp = a.groups;
   // this CTA's tiles of each group, and the CTAs with tiles in each group
   const int T0 = sweep_group_tiles(a, 0), T1 = n_grp > 1 ? sweep_group_tiles(a, 1) : 0;
@@ -568,12 +556,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
   } else {
     // ---------------------------------------------------------- epilogue
     const int q4 = warp & 3;                      // TMEM lanes 32 q4 .. 32 q4 + 31
-    const int wi = (warp - kSpEpiFirst) >> 2;     // 0 .. kSpEpiPerQuarter - 1
+    const int wi = (warp - kSpEpiFirst) >> 2;     // 0 .. EPQ - 1
     const uint32_t lane_base = static_cast<uint32_t>(32 * q4) << 16;
     // row jc + BN of a slice holds X_lo; BN % 8 == 0 keeps its swizzle phase
     const unsigned lo_off = static_cast<unsigned>(a.bn) * kSwK;
-    float2* stg = reinterpret_cast<float2*>(sp_smem + static_cast<size_t>(a.slots) * slot_bytes +
-                                            static_cast<size_t>(warp - kSpEpiFirst) * kSpStageBytes);
     long long seq = 0;
     bool ok = true;
     for (long long u = 0; u < n_units && ok; ++u) {
@@ -607,10 +593,10 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
         const uint32_t tacc = tmem + lane_base + static_cast<uint32_t>(b * a.acc_cols);
         const uint32_t par = static_cast<uint32_t>((seq >> 1) & 1);
         bool landed = false;
-#define STO_SWEEP_TILE(ST_, STAGED_)                                                                    \
-  landed = sweep_tile_update<ST_, STAGED_>(a, stg, tacc, tn, k, row_ok, xk, kchunk, drive, t, sample, Xn, \
-                                           lo_off, wi, lane, &acc_full[b], par, abort_flag)
-        if (a.staged) {
+#define STO_SWEEP_TILE(ST_, STAGED_)                                                                 \
+  landed = sweep_tile_update<ST_, (STAGED_) && EPQ == 3, EPQ>(a, tacc, tn, k, row_ok, xk, kchunk, drive, t, sample, Xn, \
+                                                lo_off, wi, &acc_full[b], par, abort_flag)
+        if (EPQ == 3 && a.staged) {
           switch (st) {
             case 0: STO_SWEEP_TILE(0, true); break;
             case 1: STO_SWEEP_TILE(1, true); break;
@@ -653,12 +639,41 @@ __global__ void __launch_bounds__(kSpThreads, 1) sweep_persistent_kernel(const _
   }
 }
 
-// X of the current stage from the stage state (ms) of every pair.
-__global__ void sweep_publish_kernel(const float2* ms, __nv_bfloat16* Xs, int N, int R, int Kpad, int bn) {
+template <int EPQ>
+__global__ void __launch_bounds__(sp_threads<EPQ>(), 1) sweep_persistent_kernel(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(1024) unsigned char sp_smem_raw[];
+  sweep_cta<EPQ>(a, blockIdx.x, gridDim.x, sp_smem_raw);
+}
+
+// A whole parameter sweep in one cooperative launch: CTAs [0, sweep_ctas)
+// run the shared-W reservoirs (sweep_cta, tensor-core product and update),
+// the CTAs after them the own-W group's lanes (group_cta, the stepper
+// engine).  Both roles run 512 threads; no CTA of one role waits for one of
+// the other, and each role's waits are the ones of its lone launch.
+struct SweepGroupArgs {
+  SweepArgs sw;
+  GroupArgs grp;
+  int sweep_ctas;
+};
+static_assert(sp_threads<3>() == kThreads, "the sweep's 512-thread form has the stepper's block shape");
+
+__global__ void __launch_bounds__(kThreads, 1) sweep_group_kernel(const __grid_constant__ SweepGroupArgs f) {
+  // 128-byte alignment, as the stepper engine's: sweep_cta aligns its ring to
+  // 1024 B inside the region (the plan's slack), so the static part stays small
+  extern __shared__ __align__(128) unsigned char sg_smem_raw[];
+  const int c = static_cast<int>(blockIdx.x);
+  if (c < f.sweep_ctas)
+    sweep_cta<3>(f.sw, c, f.sweep_ctas, sg_smem_raw);
+  else
+    group_cta(f.grp, c - f.sweep_ctas);
+}
+
+// X of stage 0 of the next RK4 step from m_n (mn, component x) of every pair.
+__global__ void sweep_publish_kernel(const float2* mn, __nv_bfloat16* Xs, int N, int R, int Kpad, int bn) {
   const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (idx >= static_cast<long long>(R) * N) return;
   const int r = static_cast<int>(idx / N), k = static_cast<int>(idx % N);
-  const float x = ms[idx].x;
+  const float x = mn[idx].x;
   const __nv_bfloat16 xh = __float2bfloat16_rn(x);
   const __nv_bfloat16 xl = __float2bfloat16_rn(x - __bfloat162float(xh));
   Xs[xt_offset(r, k, Kpad, bn)] = xh;

@@ -55,7 +55,8 @@ class sto_batch_plan(ctypes.Structure):
     _fields_ = [("tile_n", ctypes.c_int32), ("slots", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("tiles", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("tuned", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("tuned_us_per_stage", ctypes.c_float),
-                ("staged", ctypes.c_int32), ("groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("staged", ctypes.c_int32), ("groups", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
@@ -110,10 +111,13 @@ SIGNATURES = {
     "sto_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32]),
     "sto_batch_set_plan_ex": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
     "sto_batch_set_plan_staged": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    "sto_batch_set_plan_threads": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32, _I32]),
     "sto_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(sto_batch_plan)]),
     "sto_run_group": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_set_tableau": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
     "sto_group_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, ctypes.POINTER(_VP)]),
+    "sto_group_create_ex": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, _I32, ctypes.POINTER(_VP)]),
+    "sto_run_sweep_group": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, ctypes.POINTER(_VP)]),
     "sto_group_run": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(_VP)]),
     "sto_group_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sto_group_destroy": (None, [_VP]),
@@ -343,12 +347,14 @@ class Group:
     """Reservoirs with their own W advanced by one persistent launch per call
     (lanes of CTAs run members side by side; see sto_group_create)."""
 
-    def __init__(self, reservoirs, lanes: int = 0):
+    def __init__(self, reservoirs, lanes: int = 0, ctas: int = 0):
+        """ctas: CTAs the lanes occupy (0 = one per SM); fewer leave SMs to a
+        sweep run beside the group by run_sweep_group."""
         self.reservoirs = list(reservoirs)  # keeps the handles alive
         n = len(self.reservoirs)
         hs = (_VP * n)(*[r.handle for r in self.reservoirs])
         g = _VP()
-        _check(load_library().sto_group_create(hs, n, int(lanes), ctypes.byref(g)))
+        _check(load_library().sto_group_create_ex(hs, n, int(lanes), int(ctas), ctypes.byref(g)))
         self.handle = g.value
 
     def run(self, u, T=None, states_out=None):
@@ -390,6 +396,25 @@ class Group:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def run_sweep_group(sweep, group, u, T=None, sweep_states=None, group_states=None):
+    """A Sweep (shared W) and a Group (own W) advanced over the same input
+    series by one persistent launch (sto_run_sweep_group)."""
+    if T is None:
+        T = int(u.shape[0])
+    n = len(group.reservoirs)
+    pu, ku = _ptr(u, np.float32)
+    ps, ks = _ptr(sweep_states, np.float32)
+    keep, outs = [], None
+    if group_states is not None:
+        ptrs = []
+        for so in group_states:
+            p, k = _ptr(so, np.float32)
+            ptrs.append(p)
+            keep.append(k)
+        outs = (_VP * n)(*ptrs)
+    _check(load_library().sto_run_sweep_group(sweep.handle, group.handle, pu, int(T), ps, outs))
 
 
 def sto_get_info(h) -> dict:
@@ -662,11 +687,12 @@ class Sweep:
         _check(load_library().sto_batch_get_state(self.handle, out.ctypes.data))
         return out
 
-    def set_plan(self, tile_n: int = 0, slots: int = 0, groups: int = 1, staged: int = -1):
-        """Force a tile width / ring depth / reservoir-group count and staging
-        mode (1, 0, or -1 = when it fits), or (0, 0) to run the autotuner."""
-        _check(load_library().sto_batch_set_plan_staged(self.handle, int(tile_n), int(slots), int(groups),
-                                                        int(staged)))
+    def set_plan(self, tile_n: int = 0, slots: int = 0, groups: int = 1, staged: int = -1, threads: int = 512):
+        """Force a tile width / ring depth / reservoir-group count, staging
+        mode (1, 0, or -1 = choose) and threads per CTA (512 or 1024), or
+        (0, 0) to run the autotuner."""
+        _check(load_library().sto_batch_set_plan_threads(self.handle, int(tile_n), int(slots), int(groups),
+                                                         int(staged), int(threads)))
 
     def plan(self) -> dict:
         p = sto_batch_plan()

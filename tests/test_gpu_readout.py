@@ -130,3 +130,54 @@ def test_readout_learns_and_matches_oracle_on_reservoir_states():
     assert abs(n_gpu - n_gpu_orc) <= 1e-9
     assert n_orc < 0.6 and n_gpu < 0.6, (n_orc, n_gpu)
     assert abs(n_gpu - n_orc) <= 1e-3, (n_gpu, n_orc)
+
+
+def golden_readout():
+    import os
+    nmse, states = {}, {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "readout_n1000_t10000.txt")
+    with open(path) as fh:
+        for line in fh:
+            f = line.split()
+            if f and f[0] == "nmse":
+                nmse[(int(f[1]), float(f[2]))] = float(f[3])
+            elif f and f[0] == "s":
+                states[(int(f[1]), int(f[2]))] = float(f[3])
+    return nmse, states
+
+
+def test_readout_full_configuration_n1000_t10000():
+    """The plain-method readout workload at full size: N = 1000, Gaussian W,
+    10^4 input samples of 100 RK4 steps, A_in = 30 Oe, x sampled, delay-5
+    recall, washout 100, first half trains / second half scores, beta_rel =
+    0.1; expected values from the FP64 oracle
+    (tests/golden/make_readout_n1000_t10000.py).
+
+    * Over the first 200 samples the trajectory is pointwise: the states of
+      every 50th oscillator agree to 1e-4.
+    * Over 10^4 samples the reservoir is chaotic, so the NMSE is a property
+      of the ensemble of equally valid trajectories: the oracle ran from six
+      initial states within 1e-7 of each other.  The GPU's NMSE must lie
+      within 1e-3 of the interval those six NMSEs span, widened by the
+      interval's own width (the spread the FP64 oracle shows against itself).
+    * Both sides learn the task: every NMSE is below 0.85 (the mean of the
+      target scores 1)."""
+    from oracle import readout
+    from paper_2312_01121_b300 import sto
+    nmse, states = golden_readout()
+    N, T, beta = 1000, 10000, 0.1
+    W, w_in, m0, u = make_system(N, "gauss", seed=0, T=T)
+    P = sto.Params(substeps=100, A_in=30.0)
+    _, st = run_gpu(P, W, w_in, m0, u)
+    got = np.array([st[t, i] for (t, i) in states])
+    assert len(got) == 200 * 20
+    assert np.max(np.abs(got - np.array(list(states.values())))) <= 1e-4
+    y = sto.delay_target(u, 5)
+    _, n_gpu = sto.readout_evaluate(st, y, washout=100, beta_rel=beta)
+    _, n_same = readout.evaluate(st, u, washout=100, delay=5, beta_rel=beta)
+    assert abs(n_gpu - n_same) <= 1e-9
+    ens = np.array([nmse[(k, beta)] for k in range(6)])
+    lo, hi = float(ens.min()), float(ens.max())
+    assert hi < 0.85 and n_gpu < 0.85, (ens, n_gpu)
+    width = hi - lo
+    assert lo - 1e-3 - width <= n_gpu <= hi + 1e-3 + width, (n_gpu, ens)

@@ -199,21 +199,53 @@ def test_sweep_autotuner_and_invalid_plans(sto):
         plan = sw.plan()
         assert plan["tuned"] == 1 and plan["candidates"] >= 1 and plan["tuned_us_per_stage"] > 0
         assert plan["tile_n"] % 8 == 0 and plan["grid"] <= torch.cuda.get_device_properties(0).multi_processor_count
-        assert plan["groups"] in (1, 2)
+        assert plan["groups"] in (1, 2) and plan["threads"] in (512, 1024)
         # the tuner restored the state it ran from: same samples as a forced plan
         ref = np.zeros_like(st)
         with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw2:
-            sw2.set_plan(plan["tile_n"], plan["slots"], plan["groups"], plan["staged"])
+            sw2.set_plan(plan["tile_n"], plan["slots"], plan["groups"], plan["staged"], plan["threads"])
             sw2.run(u, ref)
         assert np.array_equal(st, ref)
     with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as sw:
-        with pytest.raises(sto.StoError):
-            sw.set_plan(128, 2, 1, 1)  # staging does not fit beside two 96 KB slots
+        with pytest.raises(sto.StoError) as e:
+            sw.set_plan(40, 2, 1, 1, threads=1024)  # 64 registers leave no room to load ahead
+        assert e.value.code == sto.STO_ENOTSUP
+        with pytest.raises(sto.StoError) as e:
+            sw.set_plan(40, 2, 1, 0, threads=768)  # 512 or 1024 threads
+        assert e.value.code == sto.STO_EINVAL
         with pytest.raises(sto.StoError):
             sw.set_plan(64, 3, 1, 2)  # staging mode outside -1..1
-        for staged in (0, 1):
-            sw.set_plan(40, 2, 1, staged)
-            assert sw.plan()["staged"] == staged
+        for staged, threads in ((0, 512), (1, 512), (0, 1024)):
+            sw.set_plan(40, 2, 1, staged, threads)
+            assert (sw.plan()["staged"], sw.plan()["threads"]) == (staged, threads)
+
+
+@pytest.mark.parametrize("N,R,tile_n,slots,groups", [(300, 70, 16, 3, 1), (300, 70, 40, 2, 2),
+                                                     (2500, 512, 40, 3, 2)])
+def test_sweep_threads_and_staging_bitwise_equal(sto, N, R, tile_n, slots, groups):
+    """512 threads with the next pair loaded ahead, 512 without, and 1024
+    threads run the same per-pair arithmetic on the same products: the
+    samples and the end state are the same bits, and they match the oracle."""
+    T = 2
+    W, w_in, _, u = make_system(N, "gauss", seed=17, T=T)
+    rng = np.random.default_rng(17)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    P = sto.Params(substeps=3, A_cp=100.0, A_in=30.0)
+    outs = []
+    for staged, threads in ((1, 512), (0, 512), (0, 1024)):
+        st = np.zeros((T, R, N), np.float32)
+        with sto.Sweep(W, w_in, P, currents=cur) as sw:
+            sw.set_plan(tile_n, slots, groups, staged, threads)
+            sw.run(u, st)
+            outs.append((st, sw.state()))
+    for st, m in outs[1:]:
+        assert np.array_equal(st, outs[0][0]) and np.array_equal(m, outs[0][1])
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, R // 2, R - 1):
+        OP = oracle_params(P.replace(current=float(cur[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(outs[0][0][:, r] - ref)) <= 1e-5, r
 
 
 @pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3),
@@ -338,3 +370,78 @@ def test_sweep_full_configuration_sampled_reservoirs(sto):
         OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
         _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=16)
         assert np.max(np.abs(st[:, r] - ref)) <= 1e-5, r
+
+
+def test_sweep_replan_after_a_run_continues_exactly(sto):
+    """A plan set between two calls (other group count and thread count)
+    continues from m_n: the samples equal one call under the first plan."""
+    N, R, T = 300, 70, 4
+    W, w_in, _, u = make_system(N, "gauss", seed=19, T=T)
+    cur = np.random.default_rng(19).uniform(1e-3, 3e-3, R)
+    P = sto.Params(substeps=3, A_cp=100.0, A_in=30.0)
+    s1, s2 = np.zeros((2, R, N), np.float32), np.zeros((2, R, N), np.float32)
+    with sto.Sweep(W, w_in, P, currents=cur) as sw:
+        sw.set_plan(40, 2, 1, 1, 512)
+        sw.run(u[:2], s1)
+        sw.set_plan(40, 3, 2, 0, 1024)
+        sw.run(u[2:], s2)
+    ref = np.zeros((T, R, N), np.float32)
+    with sto.Sweep(W, w_in, P, currents=cur) as sw:
+        sw.set_plan(40, 2, 1, 1, 512)
+        sw.run(u, ref)
+    assert np.array_equal(np.concatenate([s1, s2]), ref)
+
+
+def test_sweep_and_group_in_one_launch_equal_their_own_calls(sto):
+    """One cooperative launch (sto_run_sweep_group): the shared-W sweep on the
+    SMs the own-W group leaves free, the group's lanes on the others.  Each
+    part gives the same bits as its own call (sto_run_batched with the same
+    tile width, sto_group_run of a group made for the same CTAs), and the
+    oracle's states; the sweep's own plan is left as it was."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, R, T = 300, 70, 2
+    W, w_in, _, u = make_system(N, "gauss", seed=31, T=T)
+    rng = np.random.default_rng(31)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=3, A_cp=100.0, A_in=30.0)
+    Ns = [100, 257, 513, 1000, 130]
+    systems = [make_system(n, "gauss", seed=40 + i, T=1) for i, n in enumerate(Ns)]
+
+    def make():
+        sw = sto.Sweep(W, w_in, P, currents=cur, gains=gain)
+        sw.set_plan(40, 2, 2, 1, 512)
+        res = [sto.Reservoir(Wi, wi, P, m0=mi) for (Wi, wi, mi, _) in systems]
+        grp = sto.Group(res, lanes=2, ctas=sms - 24)
+        return sw, res, grp
+
+    sw, res, grp = make()
+    plan_before = sw.plan()
+    st_sw = np.zeros((T, R, N), np.float32)
+    st_g = [np.zeros((T, n), np.float32) for n in Ns]
+    sto.run_sweep_group(sw, grp, u, sweep_states=st_sw, group_states=st_g)
+    assert sw.plan() == plan_before
+    info = grp.info()
+    assert info["lanes"] * info["lane_width"] <= sms - 24
+    sw2, res2, grp2 = make()
+    ref_sw = np.zeros_like(st_sw)
+    sw2.run(u, ref_sw)
+    ref_g = [np.zeros((T, n), np.float32) for n in Ns]
+    grp2.run(u, states_out=ref_g)
+    assert np.array_equal(st_sw, ref_sw)
+    assert np.array_equal(sw.state(), sw2.state())
+    for a, b_, r1, r2 in zip(st_g, ref_g, res, res2):
+        assert np.array_equal(a, b_)
+        assert np.array_equal(r1.state(), r2.state())
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, 41, 69):
+        OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(st_sw[:, r] - ref)) <= 1e-5, r
+    for (Wi, wi, mi, _), st in zip(systems, st_g):
+        _, ref = oracle.run(oracle_params(P), Wi.astype(np.float64), wi.astype(np.float64),
+                            mi.astype(np.float64), u.astype(np.float64), nthreads=8)
+        assert np.max(np.abs(st - ref)) <= 1e-5
+    for obj in [grp, grp2, sw, sw2] + res + res2:
+        obj.close()
