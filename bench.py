@@ -64,6 +64,7 @@ def parse():
                     help="tile_n,slots[,groups[,staged[,threads]]] of the sweep kernel (default: autotuned)")
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-readout", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
     ap.add_argument("--group-lanes", type=int, default=0, help="lanes of the group launch (0 = auto)")
@@ -496,6 +497,29 @@ def time_fused(args, seed, torch, sto, dev):
     return out
 
 
+def time_readout(args, seed, torch, sto, dev):
+    """The ridge readout on the GPU (fit on the first half after a washout of
+    100, NMSE on the second half) for states of the readout workload's shape:
+    10^4 samples x N = 1000 (synthetic FP32 states; the cost does not depend
+    on their values).  Set-up work, outside every timed step."""
+    T, N = 10000, args.adj_n
+    g = torch.Generator(device=dev).manual_seed(seed)
+    states = torch.rand((T, N), generator=g, device=dev, dtype=torch.float32) * 2 - 1
+    y = torch.rand((T,), generator=g, device=dev, dtype=torch.float64)
+    (a, b), (c, d) = sto.readout_split(T, 100)
+    stream = torch.cuda.current_stream()
+    w = torch.empty(N + 1, dtype=torch.float64, device=dev)
+    sto.sto_readout_fit(states, y, a, b, 0.1, w_out=w, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sto.sto_readout_fit(states, y, a, b, 0.1, w_out=w, stream=stream)
+    t1 = time.perf_counter()
+    sto.sto_readout_nmse(states, w, y, c, d, stream=stream)
+    t2 = time.perf_counter()
+    return {"N": N, "samples": T, "train": b - a, "fit_ms": (t1 - t0) * 1e3, "nmse_ms": (t2 - t1) * 1e3,
+            "note": "FP64 Gram matrix, blocked Cholesky and solves on the GPU; wall time of one call"}
+
+
 def time_fp64(args, seed, torch, sto, dev, hbm_peak):
     """The paper's own benchmark in its precision (Sec. 3.3, Table 1): FP64
     coupling, u = 0, Eq. (initial) for every oscillator, W of the paper's
@@ -627,6 +651,9 @@ def summary(line, hbm_peak):
     grp = line.get("group")
     if grp:
         out.update({"group_us_per_stage": grp["us_per_stage"], "group_frac_hbm": grp["frac_of_hbm"]})
+    ro = line.get("readout")
+    if ro:
+        out["readout_fit_ms_n1000_t1e4"] = ro["fit_ms"]
     fu = line.get("sweep_and_group_one_launch")
     if fu and "us_per_stage" in fu:
         out.update({"sweep_and_group_one_launch_us_per_stage": fu["us_per_stage"],
@@ -673,6 +700,9 @@ def main():
     group = None
     if not args.no_group:
         group = time_group(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
+    readout = None
+    if not args.no_readout:
+        readout = time_readout(args, replica_seed(rank), torch, sto, dev)
     fused = None
     if not args.no_fused:
         fused = time_fused(args, replica_seed(rank), torch, sto, dev)
@@ -772,6 +802,8 @@ def main():
         line["sweep"] = sweep
     if group is not None:
         line["group"] = group
+    if readout is not None:
+        line["readout"] = readout
     if fused is not None:
         if sweep is not None and group is not None:
             fused["separate_launches_us_per_stage"] = sweep["us_per_stage"] + group["us_per_stage"]
