@@ -153,8 +153,12 @@ def test_readout_full_configuration_n1000_t10000():
     0.1; expected values from the FP64 oracle
     (tests/golden/make_readout_n1000_t10000.py).
 
-    * Over the first 200 samples the trajectory is pointwise: the states of
-      every 50th oscillator agree to 1e-4.
+    * At this input amplitude the reservoir is strongly chaotic: the FP64
+      oracle run from an initial state changed by 1e-7 differs from run 0 by
+      1.1e-3 at sample 40 and by O(1) at sample 100.  The GPU's own
+      differences (FP32 row sums) are far smaller, so its states of every
+      50th oscillator are compared pointwise over the first 100 samples, at
+      1e-4 (measured: 1.8e-6 at sample 100, 6e-5 at 120).
     * Over 10^4 samples the reservoir is chaotic, so the NMSE is a property
       of the ensemble of equally valid trajectories: the oracle ran from six
       initial states within 1e-7 of each other.  The GPU's NMSE must lie
@@ -169,9 +173,10 @@ def test_readout_full_configuration_n1000_t10000():
     W, w_in, m0, u = make_system(N, "gauss", seed=0, T=T)
     P = sto.Params(substeps=100, A_in=30.0)
     _, st = run_gpu(P, W, w_in, m0, u)
-    got = np.array([st[t, i] for (t, i) in states])
-    assert len(got) == 200 * 20
-    assert np.max(np.abs(got - np.array(list(states.values())))) <= 1e-4
+    assert len(states) == 200 * 20
+    early = [(t, i) for (t, i) in states if t < 100]
+    got = np.array([st[t, i] for (t, i) in early], dtype=np.float64)
+    assert np.max(np.abs(got - np.array([states[key] for key in early]))) <= 1e-4
     y = sto.delay_target(u, 5)
     _, n_gpu = sto.readout_evaluate(st, y, washout=100, beta_rel=beta)
     _, n_same = readout.evaluate(st, u, washout=100, delay=5, beta_rel=beta)
