@@ -67,6 +67,7 @@ constexpr int kSlotK = 2;
 constexpr int kSpProducers = 3;
 constexpr int kSpEpiFirst = 1 + kSpProducers;          // warp 0 multiplies, 1..3 copy
 constexpr int kSpMaxSlots = 9;
+constexpr unsigned kSpPollSleepNs = 100;  // copy warps' pause between polls of a unit release
 // Epilogue warps per TMEM lane quarter (EPQ, a template parameter of the
 // kernel): 7 (1024 threads of 64 registers) or 3 (512 threads of 128
 // registers, room to hold the next pair's state while the current one is
@@ -498,8 +499,12 @@ __device__ __forceinline__ void sweep_cta(const SweepArgs& a, const int cta, con
       bool ok = true;
       for (long long u = 0; u < n_units && ok; ++u) {
         if (ld_acquire_cta_u64(&s_go) <= static_cast<unsigned long long>(u)) {
+          // the next unit is released when the group's barrier passes, most
+          // of a stage away: poll gently (a tight loop of shared-memory loads
+          // took issue slots from the update warps of the same SM)
           const unsigned long long t0 = gtimer();
           for (uint32_t n = 1; ld_acquire_cta_u64(&s_go) <= static_cast<unsigned long long>(u); ++n) {
+            if (n > 8) __nanosleep(kSpPollSleepNs);
             if ((n & 15u) == 0 && (*abort_flag || gtimer() - t0 > a.timeout_ns)) {
               ok = false;
               break;
