@@ -588,6 +588,21 @@ def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
     return {"value": N * steps / dt, "steps": steps, "seconds": dt, "cores": nthreads}
 
 
+def workload_config(args, world):
+    """The workload the line's metric is measured on (both arms)."""
+    N, ips, S = args.n, args.ips, args.substeps
+    return {
+        "workload": f"plain single reservoir, N={N}, dense Gaussian FP32 W (std 0.1/sqrt(N), "
+                    f"zero diagonal, {4 * N * N / 1e6:.0f} MB), u~U[0,1], RK4 dt=1e-11 s, "
+                    f"{S} substeps per input sample, states sampled every sample",
+        "N": N, "input_samples_per_step": ips, "rk4_steps_per_step": ips * S,
+        "stages_per_step": 4 * S * ips, "parallelism": "replicas" if world > 1 else "single",
+        "l2": f"inputs larger than L2: W ({4 * N * N / 1e6:.0f} MB) > L2 (126 MB), no flush; by design "
+              "a 110 MB slice of W stays in L2 across stages and the panel order alternates, the "
+              "rest is re-read from HBM every stage",
+    }
+
+
 def reference_arm(args):
     """The FP64 CPU oracle as the comparison arm, on this host's cores."""
     rank, world, _ = dist_env()
@@ -616,12 +631,12 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"plain single reservoir N={N}, dense Gaussian FP32 W "
-                                   "(std 0.1/sqrt(N)); oracle step = 1 RK4 step (4 stages)",
-                       "N": N, "dt": 1e-11},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": nthreads,
                              "kind": "oracle",
-                             "sample": f"{args.steps} RK4 steps of N={N} (one per step)"},
+                             "sample": f"each step is 1 RK4 step of the same N={N} workload (the "
+                                       f"oracle's rate is per node-update, like the GPU arm's); "
+                                       f"{args.steps} timed steps"},
             "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -747,17 +762,8 @@ def main():
         "dtype_detail": "FP32 W and coupling matvec (FP32 accumulate); double-float (two FP32, "
                         "~48-bit) per-oscillator torque and RK4 combine; FP64 state between calls",
         "data": "synthetic",
-        "config": {
-            "workload": f"plain single reservoir, N={N}, dense Gaussian FP32 W (std 0.1/sqrt(N), "
-                        f"zero diagonal, {4 * N * N / 1e6:.0f} MB), u~U[0,1], RK4 dt=1e-11 s, "
-                        f"{S} substeps per input sample, states sampled every sample",
-            "N": N, "input_samples_per_step": ips, "rk4_steps_per_step": ips * S,
-            "stages_per_step": stages, "parallelism": "replicas" if world > 1 else "single",
-            "l2": f"inputs larger than L2: W ({4 * N * N / 1e6:.0f} MB) > L2 (126 MB), no flush; by design "
-                  "a 110 MB slice of W stays in L2 across stages and the panel order alternates, the "
-                  "rest is re-read from HBM every stage",
-            "plan": main_r["info"],
-        },
+        "config": workload_config(args, world),
+        "plan": main_r["info"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "frac_dram": (traffic / mean_launch_s / 1e9 / peak) if traffic else None,
