@@ -164,16 +164,16 @@ __device__ __forceinline__ void sweep_increment(const KArgs& c, df hs0, const df
 // (the next stage 0 starts from it).  Offsets are 32-bit: the batch keeps
 // R N <= 2^29, so 3 R N and the X extent stay below 2^31.
 template <int ST>
-__device__ __forceinline__ void sweep_pair(const SweepArgs& a, unsigned r, unsigned idx, unsigned RN,
+__device__ __forceinline__ void sweep_pair(const SweepArgs& a, df hs0, df ain_g, unsigned idx, unsigned RN,
                                            float hraw, int t, bool sample, df drive, df mn[3], df ms[3],
                                            df ks[3], __nv_bfloat16* Xn, unsigned xo, unsigned lo_off) {
   if constexpr (ST == 0) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) ms[i] = mn[i];
   }
-  const df hx = df_fma(a.ain_g_r[r], drive, df_mul_f(a.c.acp, hraw));
+  const df hx = df_fma(ain_g, drive, df_mul_f(a.c.acp, hraw));
   df d[3];
-  sweep_increment(a.c, a.hs0_r[r], ms, hx, d);
+  sweep_increment(a.c, hs0, ms, hx, d);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if constexpr (ST == 0) {
@@ -254,23 +254,23 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int q, int idx, i
   *tn = idx / a.tiles_m + (q == 0 ? 0 : a.tn_split);
 }
 
-// The epilogue of one tile for one epilogue warp: the pairs (reservoir
-// tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + EPQ,
-// ...  With PREF the state of the next column's pair is loaded into
-// registers while the current one is computed, and the first pair's before
-// the accumulator is waited for (the loads overlap the tile's MMAs).  tacc
-// addresses this warp's TMEM lanes of the accumulator; xk is the X offset of
-// (jc = 0, k).  Returns false when the accumulator never filled (timeout or
-// abort).
 // The state of one pair (mn; ms and ks when ST > 0) read from the [3][R][N]
-// arrays at element idx, or zeros for a pair outside the batch.
+// arrays at element idx, and its reservoir r's H_s0 and g A_in, or zeros for
+// a pair outside the batch.  The reservoir constants are read here, with the
+// state, rather than where the update first needs them: with the ring in
+// shared memory little L1 is left, and a load issued there sat on the
+// update's dependency chain.
 struct PairState {
   df m[3], s[3], k[3];
+  df hs0, ain_g;
 };
 template <int ST>
-__device__ __forceinline__ PairState load_pair(const SweepArgs& a, unsigned RN, unsigned idx, bool ok) {
+__device__ __forceinline__ PairState load_pair(const SweepArgs& a, unsigned RN, unsigned r, unsigned idx,
+                                               bool ok) {
   PairState p;
   if (ok) {
+    p.hs0 = a.hs0_r[r];
+    p.ain_g = a.ain_g_r[r];
 #pragma unroll
     for (int qq = 0; qq < 3; ++qq) {
       const float2 x0 = a.mn[qq * RN + idx];
@@ -287,6 +287,14 @@ __device__ __forceinline__ PairState load_pair(const SweepArgs& a, unsigned RN, 
   return p;
 }
 
+// The epilogue of one tile for one epilogue warp: the pairs (reservoir
+// tn * bn + jc, oscillator k = this lane's TMEM row) for jc = wi, wi + EPQ,
+// ...  With PREF the state of the next column's pair is loaded into
+// registers while the current one is computed, and the first pair's before
+// the accumulator is waited for (the loads overlap the tile's MMAs).  tacc
+// addresses this warp's TMEM lanes of the accumulator; xk is the X offset of
+// (jc = 0, k).  Returns false when the accumulator never filled (timeout or
+// abort).
 template <int ST, bool PREF, int EPQ>
 __device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, uint32_t tacc, int tn, unsigned k,
                                                   bool row_ok, unsigned xk, unsigned kchunk, df drive, int t,
@@ -298,7 +306,7 @@ __device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, uint32_t t
   const unsigned istep = kStep * N;
   unsigned r = static_cast<unsigned>(tn * a.bn + wi), idx = r * N + k;
   PairState cur, nxt;
-  if constexpr (PREF) nxt = load_pair<ST>(a, RN, idx, row_ok && r < R);
+  if constexpr (PREF) nxt = load_pair<ST>(a, RN, r, idx, row_ok && r < R);
   const bool landed = mbar_wait_bounded(acc_bar, acc_parity, a.timeout_ns, abort_flag);
   if (!__all_sync(0xffffffffu, landed)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -309,15 +317,17 @@ __device__ __forceinline__ bool sweep_tile_update(const SweepArgs& a, uint32_t t
     const bool pair_ok = row_ok && r < R;
     if constexpr (PREF) {
       cur = nxt;
-      if (jc + static_cast<int>(kStep) < a.bn) nxt = load_pair<ST>(a, RN, idx + istep, row_ok && r + kStep < R);
+      if (jc + static_cast<int>(kStep) < a.bn)
+        nxt = load_pair<ST>(a, RN, r + kStep, idx + istep, row_ok && r + kStep < R);
     } else {
-      cur = load_pair<ST>(a, RN, idx, pair_ok);
+      cur = load_pair<ST>(a, RN, r, idx, pair_ok);
     }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const float hraw = __fadd_rn(__uint_as_float(vh), __uint_as_float(vl));
     if (pair_ok) {
       const unsigned xo = xk + static_cast<unsigned>(jc) * 64u + ((kchunk ^ (static_cast<unsigned>(jc) & 7u)) << 3);
-      sweep_pair<ST>(a, r, idx, RN, hraw, t, sample, drive, cur.m, cur.s, cur.k, Xn, xo, lo_off);
+      sweep_pair<ST>(a, cur.hs0, cur.ain_g, idx, RN, hraw, t, sample, drive, cur.m, cur.s, cur.k, Xn, xo,
+                     lo_off);
     }
   }
   return true;
