@@ -127,7 +127,8 @@ def test_group_of_own_w_reservoirs_matches_separate_runs(sto):
 
 @pytest.mark.parametrize("tile_n,slots,groups", [(16, 3, 1), (32, 4, 1), (48, 3, 1), (80, 2, 1), (80, 3, 1),
                                                  (64, 3, 1), (16, 5, 1), (112, 2, 1), (128, 2, 1), (16, 4, 2),
-                                                 (24, 3, 2), (40, 2, 2), (48, 3, 2), (32, 4, 2)])
+                                                 (24, 3, 2), (40, 2, 2), (48, 3, 2), (32, 4, 2), (24, 3, 1),
+                                                 (56, 3, 2), (8 * 7, 2, 1)])
 def test_sweep_forced_plans_match_oracle(sto, tile_n, slots, groups):
     """Every tile width, ring depth (also depths that are not a multiple of
     the three copy warps, which then own unequal numbers of slots) and group
@@ -248,7 +249,7 @@ def test_sweep_threads_and_staging_bitwise_equal(sto, N, R, tile_n, slots, group
         assert np.max(np.abs(outs[0][0][:, r] - ref)) <= 1e-5, r
 
 
-@pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3),
+@pytest.mark.parametrize("N,R,tile_n,slots", [(300, 70, 16, 3), (256, 2400, 16, 3), (2500, 512, 40, 3), (2500, 512, 24, 3),
                                               (1000, 65, 32, 4), (2500, 512, 40, 2)])
 def test_sweep_two_groups_bitwise_equal_to_one(sto, N, R, tile_n, slots):
     """Two reservoir groups with their own barriers only reorder independent
