@@ -253,6 +253,10 @@ cudaError_t launch_stepper_mode(const Plan& pl, const sto::KArgs& a, cudaStream_
   if (pl.rpw <= 1) return launch_rpw<1, false, F, kW>(pl, a, s);
   if (pl.rpw <= 2) return launch_rpw<2, false, F, kW>(pl, a, s);
   if (pl.rpw <= 4) return launch_rpw<4, false, F, kW>(pl, a, s);
+  // rows a warp does not own still cost issue slots (the FP64 FMA coupling is
+  // bound by the FP64 pipe), so N = 10^4 on 148 CTAs (68 rows, 5 per warp)
+  // gets its own width instead of 8
+  if (pl.rpw == 5) return launch_rpw<5, false, F, kW>(pl, a, s);
   if (pl.rpw <= 8) return launch_rpw<8, false, F, kW>(pl, a, s);
   return launch_rpw<16, false, F, kW>(pl, a, s);
 }
