@@ -135,7 +135,8 @@ def measured_bf16():
 # Sources whose change invalidates a recorded DRAM-traffic figure of the
 # stepper kernel (device code and the host code that plans its launch).
 STEPPER_SOURCES = ("paper_2312_01121_b300/csrc/sto_kernel.cuh", "paper_2312_01121_b300/csrc/dfloat.cuh",
-                   "paper_2312_01121_b300/csrc/stepper_plan.h", "include/sto.h")
+                   "paper_2312_01121_b300/csrc/stepper_plan.h", "paper_2312_01121_b300/csrc/sto.cu",
+                   "include/sto.h")
 TRAFFIC_FILE = os.path.join("profiles", "dram_traffic.txt")
 
 
