@@ -141,3 +141,45 @@ def test_noalloc_wrapper_checks_extents_before_the_call(lib):
         with pytest.raises(ValueError, match=name):
             sto.sto_run_noalloc(N, P, args["W"], args["w_in"], args["state"], args["u"], T,
                                 args["states_out"])
+
+
+def test_new_entry_points_reject_arguments_before_cuda(lib):
+    """The readout, row-shard, group and single-launch sweep entry points
+    check their arguments before any CUDA call (no GPU needed)."""
+    buf = (ctypes.c_float * 64)()
+    dbuf = (ctypes.c_double * 64)()
+    out = ctypes.c_double()
+    # readout: null pointers, empty or inverted ranges, negative ridge, N too large
+    assert lib.sto_readout_fit(None, 4, 2, dbuf, 0, 4, 0.1, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_fit(buf, 4, 2, None, 0, 4, 0.1, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_fit(buf, 4, 2, dbuf, 0, 4, 0.1, None, None) == sto.STO_EINVAL
+    for t0, t1 in ((-1, 2), (3, 3), (3, 2), (0, 5)):
+        assert lib.sto_readout_fit(buf, 4, 2, dbuf, t0, t1, 0.1, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_fit(buf, 4, 2, dbuf, 0, 4, -1.0, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_fit(buf, 4, 2, dbuf, 0, 4, float("nan"), dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_fit(buf, 4, 40000, dbuf, 0, 4, 0.1, dbuf, None) == sto.STO_ENOTSUP
+    assert lib.sto_readout_predict(buf, 0, 2, dbuf, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_predict(buf, 4, 2, None, dbuf, None) == sto.STO_EINVAL
+    assert lib.sto_readout_nmse(buf, 4, 2, dbuf, dbuf, 0, 4, None, None) == sto.STO_EINVAL
+    assert lib.sto_readout_nmse(buf, 4, 2, dbuf, dbuf, 2, 1, ctypes.byref(out), None) == sto.STO_EINVAL
+    # row shards: the block must lie inside [0, N)
+    cp = sto.Params().to_c()
+    h = ctypes.c_void_p()
+    for N, row0, rows in ((0, 0, 1), (8, -1, 2), (8, 0, 0), (8, 6, 3)):
+        assert lib.sto_shard_create(N, row0, rows, ctypes.byref(cp), buf, buf, None, None,
+                                    ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_shard_create(8, 0, 8, ctypes.byref(cp), None, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_shard_create(8, 0, 8, ctypes.byref(cp), buf, buf, None, None, None) == sto.STO_EINVAL
+    bad = sto.Params(substeps=0).to_c()
+    assert lib.sto_shard_create(8, 0, 8, ctypes.byref(bad), buf, buf, None, None, ctypes.byref(h)) == sto.STO_EINVAL
+    assert lib.sto_shard_stage(None, buf, 0, None, 0, buf, None) == sto.STO_EINVAL
+    assert lib.sto_shard_publish(None, buf) == sto.STO_EINVAL
+    assert lib.sto_shard_get_state_f64(None, dbuf) == sto.STO_EINVAL
+    lib.sto_shard_destroy(None)
+    # groups and the single-launch sweep
+    g = ctypes.c_void_p()
+    assert lib.sto_group_create_ex(None, 1, 0, 0, ctypes.byref(g)) == sto.STO_EINVAL
+    hs = (ctypes.c_void_p * 1)(None)
+    assert lib.sto_group_create_ex(hs, 1, 0, -1, ctypes.byref(g)) == sto.STO_EINVAL
+    assert lib.sto_run_sweep_group(None, None, buf, 1, None, None) == sto.STO_EINVAL
+    assert lib.sto_batch_set_plan_threads(None, 40, 3, 1, 0, 512) == sto.STO_EINVAL
