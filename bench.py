@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-readout", action="store_true")
+    ap.add_argument("--no-shard", action="store_true")
     ap.add_argument("--group-r", type=int, default=64)
     ap.add_argument("--group-t", type=int, default=1, help="input samples per timed group call")
     ap.add_argument("--group-lanes", type=int, default=0, help="lanes of the group launch (0 = auto)")
@@ -498,6 +499,33 @@ def time_fused(args, seed, torch, sto, dev):
     return out
 
 
+def time_shard(args, seed, torch, sto, dev, hbm_peak):
+    """The row-sharded path (one row block per GPU, an all-gather of the
+    stage values between stages) on this one GPU: a single block holding all
+    N = 10^4 rows, one stage launch per RK4 stage, one input sample replayed
+    as a CUDA graph.  What a rank's stage costs before any exchange."""
+    from paper_2312_01121_b300.shard import ShardedReservoir
+    N, S, T = args.n, args.substeps, 2
+    W, w_in, m0, u = workload(N, T + 1, seed)
+    res = ShardedReservoir(N, sto.Params(substeps=S), W_rows=torch.from_numpy(W).to(dev),
+                           w_in_rows=torch.from_numpy(w_in).to(dev), m0_rows=torch.from_numpy(m0).to(dev))
+    u_d = torch.from_numpy(u).to(dev)
+    res.run(u_d[:1], graph=True)  # capture and warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    res.run(u_d[1:], graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (4 * S * T)
+    return {"workload": f"one row block holding all N={N} rows (world size 1), {T} input samples x {S} RK4 "
+                        "steps, each sample one CUDA-graph replay of its 4 S stage launches and exchanges",
+            "us_per_stage": us, "value": N * S * T / (us * 4 * S * T / 1e6), "unit": "node-updates/s",
+            "w_gbs_algorithmic": 4.0 * N * N / (us * 1e-6) / 1e9,
+            "frac_of_hbm": 4.0 * N * N / (us * 1e-6) / 1e9 / hbm_peak}
+
+
 def time_readout(args, seed, torch, sto, dev):
     """The ridge readout on the GPU (fit on the first half after a washout of
     100, NMSE on the second half) for states of the readout workload's shape:
@@ -667,6 +695,9 @@ def summary(line, hbm_peak):
     grp = line.get("group")
     if grp:
         out.update({"group_us_per_stage": grp["us_per_stage"], "group_frac_hbm": grp["frac_of_hbm"]})
+    sh = line.get("shard")
+    if sh:
+        out["shard_n1e4_us_per_stage"] = sh["us_per_stage"]
     ro = line.get("readout")
     if ro:
         out["readout_fit_ms_n1000_t1e4"] = ro["fit_ms"]
@@ -716,6 +747,9 @@ def main():
     group = None
     if not args.no_group:
         group = time_group(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
+    shard = None
+    if not args.no_shard:
+        shard = time_shard(args, replica_seed(rank), torch, sto, dev, measured_peaks()[0])
     readout = None
     if not args.no_readout:
         readout = time_readout(args, replica_seed(rank), torch, sto, dev)
@@ -811,6 +845,8 @@ def main():
         line["group"] = group
     if readout is not None:
         line["readout"] = readout
+    if shard is not None:
+        line["shard"] = shard
     if fused is not None:
         if sweep is not None and group is not None:
             fused["separate_launches_us_per_stage"] = sweep["us_per_stage"] + group["us_per_stage"]

@@ -47,8 +47,9 @@ class CudaBlock:
     def __init__(self, N, row0, rows, params, W_rows, w_in_rows, m0_rows=None, stream=None):
         import torch
         lib = _sto.load_library()
-        # the block's launches and the exchange's copies share torch's stream
+        # the block's launches and the exchange's copies share one stream
         stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = stream
         self.N, self.row0, self.rows, self.params = int(N), int(row0), int(rows), params
         self.stream = stream
         pW, kW = _sto._ptr(W_rows, np.float32)
@@ -115,9 +116,14 @@ class ShardedReservoir:
         self.row0, self.rows = partition(self.N, self.world)[self.rank]
         self.chunk = -(-self.N // self.world)
         if block is None:
+            # a stream of its own: the stage launches and the exchange are
+            # ordered on it, and run(graph=True) captures both from it
+            stream = stream if stream is not None else torch.cuda.Stream()
             block = CudaBlock(self.N, self.row0, self.rows, params, W_rows, w_in_rows, m0_rows, stream)
             device = device or torch.device("cuda", torch.cuda.current_device())
         self.block = block
+        self.stream = getattr(block, "stream", None)
+        self._graph = None
         self.device = device or torch.device("cpu")
         dt = getattr(torch, block.dtype)
         # the gathered stage values (world chunks; entries past N stay zero)
@@ -132,22 +138,64 @@ class ShardedReservoir:
         import torch.distributed as dist
         dist.all_gather_into_tensor(self.x[:self.world * self.chunk], self.x_own, group=self.group)
 
-    def run(self, u, states_out=None):
+    def _sample(self, u_t, row):
+        """One input sample: substeps x 4 stages, each followed by the exchange."""
+        S = int(self.params.substeps)
+        for j in range(S):
+            for st in range(4):
+                flags = (SAMPLE_START if (j == 0 and st == 0) else 0) | \
+                        (SAMPLE_END if (j == S - 1 and st == 3) else 0)
+                self.block.stage(self.x, st, u_t if flags & SAMPLE_START else None, flags, self.x_own,
+                                 row if flags & SAMPLE_END else None)
+                self._exchange()
+
+    def run(self, u, states_out=None, graph: bool = False):
         """Advance over the input series u (T x n_in, a tensor on this rank's
         device); states_out (T x rows, same device) receives this block's
-        samples.  Every rank calls run with the same u."""
-        T, S = int(u.shape[0]), int(self.params.substeps)
-        self.block.publish(self.x_own)
-        self._exchange()
-        for t in range(T):
-            for j in range(S):
-                for st in range(4):
-                    flags = (SAMPLE_START if (j == 0 and st == 0) else 0) | \
-                            (SAMPLE_END if (j == S - 1 and st == 3) else 0)
-                    row = states_out[t] if (states_out is not None and flags & SAMPLE_END) else None
-                    self.block.stage(self.x, st, u[t] if flags & SAMPLE_START else None, flags,
-                                     self.x_own, row)
-                    self._exchange()
+        samples.  Every rank calls run with the same u.
+
+        graph=True (CUDA blocks): one input sample (its 4 x substeps stage
+        launches and exchanges) is captured once as a CUDA graph and replayed
+        per sample, with the sample's input and output rows copied through
+        fixed buffers; the results are the same bits."""
+        import contextlib
+
+        import torch
+        T = int(u.shape[0])
+        caller = torch.cuda.current_stream() if self.stream is not None else None
+        if caller is not None:
+            self.stream.wait_stream(caller)  # the caller's inputs first
+        ctx = torch.cuda.stream(self.stream) if self.stream is not None else contextlib.nullcontext()
+        try:
+            return self._run(u, states_out, graph, T, ctx)
+        finally:
+            if caller is not None:
+                caller.wait_stream(self.stream)  # then the caller's later work
+
+    def _run(self, u, states_out, graph, T, ctx):
+        import torch
+        with ctx:
+            self.block.publish(self.x_own)
+            self._exchange()
+            if not graph:
+                for t in range(T):
+                    self._sample(u[t], states_out[t] if states_out is not None else None)
+                return states_out
+            if self.stream is None:
+                raise ValueError("graph=True needs a CUDA block")
+            if self._graph is None:
+                self._u_buf = torch.zeros(int(self.params.n_in), dtype=torch.float32, device=self.device)
+                self._row_buf = torch.zeros(self.rows, dtype=torch.float32, device=self.device)
+                g = torch.cuda.CUDAGraph()
+                # relaxed: the library checks its pointers (cudaPointerGetAttributes)
+                with torch.cuda.graph(g, stream=self.stream, capture_error_mode="relaxed"):
+                    self._sample(self._u_buf, self._row_buf)
+                self._graph = g
+            for t in range(T):
+                self._u_buf.copy_(u[t])
+                self._graph.replay()
+                if states_out is not None:
+                    states_out[t].copy_(self._row_buf)
         return states_out
 
     def state(self) -> np.ndarray:

@@ -154,3 +154,25 @@ def test_shard_argument_errors(sto):
                                  o.data_ptr(), None)
         assert rc == sto.STO_EINVAL, (stg, fl)
     b.close()
+
+
+@pytest.mark.parametrize("N,T,S", [(1000, 4, 10), (10000, 1, 2)])
+def test_graph_replay_equals_the_launch_loop(sto, N, T, S):
+    """run(graph=True) captures one input sample (4 S stage launches and
+    exchanges) as a CUDA graph and replays it per sample: the same bits as
+    the launch loop, and the oracle's states."""
+    from paper_2312_01121_b300.shard import ShardedReservoir
+    W, w_in, m0, u = make_system(N, "gauss", seed=N + 7, T=T)
+    P = sto.Params(substeps=S, A_cp=90.0, A_in=20.0)
+    Wd, wd, md, ud = dev_arrays(W, w_in, m0, u)
+    outs = []
+    for graph in (False, True):
+        res = ShardedReservoir(N, P, W_rows=Wd, w_in_rows=wd, m0_rows=md)
+        st = torch.zeros((T, N), dtype=torch.float32, device="cuda")
+        res.run(ud, st, graph=graph)
+        torch.cuda.synchronize()
+        outs.append((st.cpu().numpy(), res.state()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    m_orc, st_orc = run_oracle(P, W, w_in, m0, u)
+    assert np.max(np.abs(outs[1][0] - st_orc)) <= 1e-5
+    assert np.max(np.abs(outs[1][1] - m_orc)) <= 1e-5
