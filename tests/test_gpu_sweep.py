@@ -446,3 +446,39 @@ def test_sweep_and_group_in_one_launch_equal_their_own_calls(sto):
         assert np.max(np.abs(st - ref)) <= 1e-5
     for obj in [grp, grp2, sw, sw2] + res + res2:
         obj.close()
+
+
+def test_whole_sweep_configuration_in_one_launch(sto):
+    """The benchmark's whole sweep in one cooperative launch
+    (sto_run_sweep_group, the split it times): 512 reservoirs sharing one
+    N = 2500 Gaussian W (I ~ U[1, 3] mA, g ~ U[0.5, 2]) beside 64 reservoirs
+    with their own Gaussian W and N ~ U[100, 4000] on 3 lanes of the other
+    SMs; sampled reservoirs of both kinds against the oracle (1e-5)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, R, T = 2500, 512, 1
+    W, w_in, _, u = make_system(N, "gauss", seed=33, T=T)
+    rng = np.random.default_rng(33)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=3, A_cp=50.0, A_in=20.0)
+    Ns = np.random.default_rng([33, 11]).integers(100, 4001, 64)
+    systems = [make_system(int(n), "gauss", seed=500 + i, T=1) for i, n in enumerate(Ns)]
+    sw = sto.Sweep(W, w_in, P, currents=cur, gains=gain)
+    res = [sto.Reservoir(Wi, wi, P, m0=mi) for (Wi, wi, mi, _) in systems]
+    grp = sto.Group(res, lanes=0, ctas=sms - 28)
+    st_sw = np.zeros((T, R, N), np.float32)
+    st_g = [np.zeros((T, int(n)), np.float32) for n in Ns]
+    sto.run_sweep_group(sw, grp, u, sweep_states=st_sw, group_states=st_g)
+    Wb = bf16_round(W).astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in (0, 255, 511):
+        OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=16)
+        assert np.max(np.abs(st_sw[:, r] - ref)) <= 1e-5, r
+    for i in (0, int(np.argmax(Ns)), int(np.argmin(Ns)), 63):
+        Wi, wi, mi, _ = systems[i]
+        _, ref = oracle.run(oracle_params(P), Wi.astype(np.float64), wi.astype(np.float64),
+                            mi.astype(np.float64), u.astype(np.float64), nthreads=16)
+        assert np.max(np.abs(st_g[i] - ref)) <= 1e-5, i
+    for obj in [grp, sw] + res:
+        obj.close()
