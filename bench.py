@@ -674,9 +674,11 @@ def reference_arm(args):
 def summary(line, hbm_peak):
     """The secondary workloads' headline numbers in one short object, printed
     last in the line so that a truncated tail of the output still holds them."""
-    out = {"n1e4_us_per_stage": line["roofline"]["us_per_stage"],
-           "n1e4_frac_hbm_alg": line["roofline"]["frac"],
-           "n1e4_frac_hbm_dram": line["roofline"].get("frac_dram")}
+    n = line["config"]["N"]
+    tag = "n1e4" if n == 10000 else f"n{n}"  # the headline workload's size
+    out = {f"{tag}_us_per_stage": line["roofline"]["us_per_stage"],
+           f"{tag}_frac_hbm_alg": line["roofline"]["frac"],
+           f"{tag}_frac_hbm_dram": line["roofline"].get("frac_dram")}
     also = line.get("also")
     if also:
         out.update({"n1e3_node_updates_per_s": also["value"], "n1e3_us_per_stage": also["us_per_stage"],
