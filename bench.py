@@ -778,6 +778,8 @@ def main():
     if rank == 0 and not args.no_cpu:
         try:
             cpu = cpu_oracle_rate(N, args.cpu_seconds, 0, os.cpu_count() or 1)
+            # the same oracle on one host thread, a shorter sample
+            cpu["single_thread"] = cpu_oracle_rate(N, max(1.0, args.cpu_seconds / 4), 0, 1)
         except Exception as e:  # the baseline is informative, never fatal
             cpu = {"error": str(e)}
     if rank != 0:
@@ -824,6 +826,11 @@ def main():
                                     "sample": f"{cpu['steps']} RK4 steps of the same N={N} "
                                               f"workload in {cpu['seconds']:.1f} s "
                                               "(FP64 C oracle, OpenMP over matvec rows)"}
+            one = cpu.get("single_thread")
+            if one:
+                line["cpu_baseline"]["single_thread"] = {
+                    "value": one["value"], "cores": 1,
+                    "sample": f"{one['steps']} RK4 steps in {one['seconds']:.1f} s"}
         else:
             line["cpu_baseline"] = cpu
     if small is not None:
