@@ -58,7 +58,7 @@
 extern "C" {
 #endif
 
-#define STO_ABI_VERSION 3
+#define STO_ABI_VERSION 4
 
 #if defined(__GNUC__)
 #define STO_API __attribute__((visibility("default")))
@@ -109,7 +109,13 @@ typedef struct sto_config {
   int32_t timeout_ms;  /* limit of every device-side wait (default 2000) */
   int32_t l2_keep_mb;  /* W larger than L2: MB of W kept L2-resident across
                           stages (0 = default, 110 MB; -1 = none) */
-  int32_t reserved[5]; /* must be 0 */
+  int32_t tmem_w;      /* FP32 W larger than L2: 0 (default) keeps the last
+                          panels of each CTA's rows of W in the SM's tensor
+                          memory for the whole call (up to 128 columns per
+                          consumer warp: 6 panels of 68 x 128 at N = 10^4),
+                          so they are not streamed again; -1 streams every
+                          panel.  The results are the same bits. */
+  int32_t reserved[4]; /* must be 0 */
 } sto_config;
 
 /* The launch plan chosen for a handle (read-only, for tuning and reports). */
@@ -132,6 +138,9 @@ typedef struct sto_info {
                             where the polled lines fall in the L2; 0 before
                             that or otherwise) */
   int32_t xbuf_slot;     /* the placement kept (the fastest) */
+  int32_t tmem_panels;   /* panels of each CTA's rows of W held in tensor
+                            memory for the whole call (sto_config.tmem_w);
+                            0 when W is on chip, L2-resident or not FP32 */
 } sto_info;
 
 typedef struct sto_handle sto_handle; /* opaque */

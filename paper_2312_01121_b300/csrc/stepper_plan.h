@@ -15,6 +15,7 @@ namespace {
 struct Plan {
   int G = 1, R_max = 1, P = 1, ns = 1, resident = 1, rpw = 1;
   int regw = 0;  // W in registers (FP32 coupling, on chip, <= 16 rows, several CTAs, N <= 1344)
+  int tmem = 0;  // streamed FP32 W: the last panels of each row block held in tensor memory
   size_t smem = 0;
 };
 

@@ -197,9 +197,9 @@ int raise_dyn_smem_cap(F* func) {
 }
 
 template <int RPW, bool kRowMajorW = false, int kProg = sto::kProgForward, int kW = sto::kWf32,
-          bool kRegW = false>
+          bool kRegW = false, bool kTmemW = false>
 cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
-  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW>);
+  const int room = raise_dyn_smem_cap(sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW, kTmemW>);
   if (room < static_cast<int>(pl.smem)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.G);
@@ -211,7 +211,7 @@ cudaError_t launch_rpw(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW>, a);
+  return cudaLaunchKernelEx(&cfg, sto::sto_persistent_kernel<RPW, kRowMajorW, kProg, kW, kRegW, kTmemW>, a);
 }
 
 cudaError_t launch_stepper_rowmajor(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
@@ -243,12 +243,33 @@ cudaError_t launch_tableau(const Plan& pl, const sto::KArgs& a, cudaStream_t s) 
   return launch_rpw<16, false, B>(pl, a, s);
 }
 
+// Whether a forward FP32 launch holds panels in tensor memory: W streamed
+// (not on chip, not all L2-resident), at least 3 rows per warp.
+bool tmem_used(const Plan& pl, int l2_keep, int keep) {
+  return pl.tmem && !pl.resident && !l2_keep && keep < pl.P && pl.rpw > 2;
+}
+int tmem_panels_of(const Plan& pl, int l2_keep, int keep) {
+  if (!tmem_used(pl, l2_keep, keep)) return 0;
+  if (pl.rpw <= 4) return sto::tmem_panel_count<4>(pl.P, keep);
+  if (pl.rpw == 5) return sto::tmem_panel_count<5>(pl.P, keep);
+  if (pl.rpw <= 8) return sto::tmem_panel_count<8>(pl.P, keep);
+  return sto::tmem_panel_count<16>(pl.P, keep);
+}
+
 template <int kW>
 cudaError_t launch_stepper_mode(const Plan& pl, const sto::KArgs& a, cudaStream_t s) {
   constexpr int F = sto::kProgForward;
   if constexpr (kW == sto::kWf32) {
     if (pl.regw) return pl.rpw <= 1 ? launch_rpw<1, false, F, kW, true>(pl, a, s)
                                     : launch_rpw<2, false, F, kW, true>(pl, a, s);
+    // W streamed from HBM (not all of it L2-resident): the last panels of
+    // each row block stay in tensor memory
+    if (tmem_used(pl, a.l2_keep, a.keep_panels)) {
+      if (pl.rpw <= 4) return launch_rpw<4, false, F, kW, false, true>(pl, a, s);
+      if (pl.rpw == 5) return launch_rpw<5, false, F, kW, false, true>(pl, a, s);
+      if (pl.rpw <= 8) return launch_rpw<8, false, F, kW, false, true>(pl, a, s);
+      return launch_rpw<16, false, F, kW, false, true>(pl, a, s);
+    }
   }
   if (pl.rpw <= 1) return launch_rpw<1, false, F, kW>(pl, a, s);
   if (pl.rpw <= 2) return launch_rpw<2, false, F, kW>(pl, a, s);
@@ -624,8 +645,9 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
   int rc = check_params(params);
   if (rc) return rc;
   if (cfg) {
-    if (cfg->grid < 0 || cfg->timeout_ms < 0 || cfg->l2_keep_mb < -1) return STO_EINVAL;
-    for (int i = 0; i < 5; ++i)
+    if (cfg->grid < 0 || cfg->timeout_ms < 0 || cfg->l2_keep_mb < -1 || cfg->tmem_w < -1 || cfg->tmem_w > 0)
+      return STO_EINVAL;
+    for (int i = 0; i < 4; ++i)
       if (cfg->reserved[i] != 0) return STO_EINVAL;
   }
   if (N > (1LL << 20)) return STO_ENOTSUP;
@@ -654,6 +676,8 @@ int create_impl(int64_t N, const sto_params* params, const void* W, int wmode, c
     return fail(cuda_fail(e));
   rc = make_plan(N, cfg ? cfg->grid : 0, h->sm_count, static_cast<size_t>(smem_optin), &h->plan, wmode);
   if (rc) return fail(rc);
+  // streamed FP32 W keeps its last panels in tensor memory (launch_stepper_mode)
+  h->plan.tmem = (wmode == sto::kWf32 && !h->plan.resident && !(cfg && cfg->tmem_w < 0)) ? 1 : 0;
 
   const int n_in = params->n_in;
   const size_t wt_elems = static_cast<size_t>(N) * h->plan.P * sto::kPanelCols;
@@ -908,6 +932,9 @@ int sto_get_info(const sto_handle* h, sto_info* out) {
   out->w_bytes = w_elem_bytes(h->wmode) * h->N * h->N;
   out->xbuf_timed = h->xbuf_timed;
   out->xbuf_slot = h->xbuf_slot;
+  if (h->wmode == sto::kWf32)
+    out->tmem_panels = tmem_panels_of(h->plan, l2_keeps(h->N),
+                                      keep_panels(h->N, h->plan.P, h->l2_keep_mb));
   return STO_OK;
 }
 

@@ -803,6 +803,34 @@ struct RowSums<kWf32, RPW> {
       }
     }
   }
+  // The same panel with this thread's W values read from tensor memory
+  // (kTmemW): row q's four at columns taddr + 4 q of its lane.  The FMAs
+  // are those of panel(), in the same order.
+  __device__ __forceinline__ void panel_tmem(uint32_t taddr, const float* xs, int j, int warp, int lane, int R) {
+    const float4 xv = reinterpret_cast<const float4*>(xs)[j * (kPanelCols / 4) + lane];
+    uint32_t w[RPW][4];
+    __syncwarp();  // the loads below are warp-aligned
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0u;
+      if (warp + q * kConsWarps < R)  // the same for every lane of the warp
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[q][0]), "=r"(w[q][1]), "=r"(w[q][2]), "=r"(w[q][3])
+                     : "r"(taddr + 4u * q));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (warp + q * kConsWarps < R) {
+        float v = s[q];
+        v = fmaf(__uint_as_float(w[q][0]), xv.x, v);
+        v = fmaf(__uint_as_float(w[q][1]), xv.y, v);
+        v = fmaf(__uint_as_float(w[q][2]), xv.z, v);
+        v = fmaf(__uint_as_float(w[q][3]), xv.w, v);
+        s[q] = v;
+      }
+    }
+  }
   __device__ __forceinline__ void store(float* hs, int warp, int lane, int R) {
     // butterfly sums of all rows at once (rows past R hold 0), so the
     // shuffle chains of different rows overlap
@@ -929,8 +957,29 @@ struct RowSums<kWf64, RPW> {
 // barrier per stage remains (before the owners add the warps' partials);
 // warp 0 holds no columns, so its owners' work after publishing never
 // delays a poll.
-template <int RPW, bool kRowMajorW, int kProg, int kW, bool kRegW = false>
+// W panels held in tensor memory (kTmemW: FP32 coupling, W streamed).  The
+// engine has no use for the SM's 256 KB of tensor memory otherwise, so each
+// consumer thread keeps its rows' four columns of a few streamed panels of
+// its row block there for the whole launch.  Those panels are never copied
+// again, and DRAM moves that many fewer bytes per stage.  They are taken
+// from the middle of the streamed panels [keep_panels, P): the panels next
+// to either end are the ones the alternating panel order already finds in
+// L2 at a stage boundary.
+// Tensor memory is 128 lanes x 512 columns of 32 bits; a warp reaches only
+// the 32 lanes of its quarter (warp % 4), so the four warps of a quarter
+// take 128 columns each (warp / 4).  A panel costs a thread 4 RPW columns.
+constexpr int kTmemAllocCols = 512;
+constexpr int kTmemWarpCols = 128;
+template <int RPW>
+__device__ __host__ __forceinline__ int tmem_panel_count(int P, int keep_panels) {
+  const int fit = kTmemWarpCols / (4 * RPW), streamed = P - keep_panels;
+  return fit < streamed ? fit : (streamed > 0 ? streamed : 0);
+}
+
+template <int RPW, bool kRowMajorW, int kProg, int kW, bool kRegW = false, bool kTmemW = false>
 __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, const int G) {
+  static_assert(!kTmemW || (kW == kWf32 && !kRowMajorW && !kRegW && kTmemWarpCols / (4 * RPW) >= 1),
+                "tensor-memory panels: FP32 coupling, tiled W, streamed");
   extern __shared__ __align__(128) unsigned char smem[];
   const int q = a.N / G, rem = a.N % G;
   const int R = q + (c < rem ? 1 : 0);
@@ -949,6 +998,13 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
   uint64_t* full = reinterpret_cast<uint64_t*>(part + (colsplit ? kConsWarps * kColSplitRows : 0));
   uint64_t* empty = full + a.ns;
   volatile int* s_abort = reinterpret_cast<volatile int*>(empty + a.ns);
+  // beside the abort flag, in the 16 bytes the plan keeps after the barriers
+  [[maybe_unused]] uint32_t* s_tmem = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(empty + a.ns) + 4);
+  // panels [t0, t0 + Pt) of the row block live in tensor memory (kTmemW);
+  // the other Ps panels are streamed
+  const int Pt = kTmemW ? tmem_panel_count<RPW>(a.P, a.keep_panels) : 0;
+  const int Ps = a.P - Pt;
+  const int t0 = kTmemW ? a.keep_panels + (a.P - a.keep_panels - Pt) / 2 : a.P;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -966,10 +1022,48 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
     // them finite (they meet x = 0)
     for (size_t i = tid; i < slot_floats * a.ns; i += kThreads) ring[i] = 0.f;
   }
+  if constexpr (kTmemW) {
+    if (warp == 0) {
+      __syncwarp();  // thread 0 initialised the barriers alone
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                   "r"(static_cast<uint32_t>(kTmemAllocCols))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
   __syncthreads();
 
   const float* Wc = a.W + static_cast<size_t>(r0) * a.P * kPanelCols;
   const uint32_t panel_bytes = static_cast<uint32_t>(R) * kPanelCols * 4u;
+  // this thread's columns of tensor memory: its warp's lane quarter and
+  // column block; panel t0 + t starts at column 4 RPW t of the block
+  [[maybe_unused]] uint32_t tmem_w = 0;
+  if constexpr (kTmemW) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_w = *s_tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+             static_cast<uint32_t>(kTmemWarpCols * (warp >> 2));
+    if (warp < kConsWarps) {
+      // fill once: this thread's four columns of each of its rows
+      for (int t = 0; t < Pt; ++t) {
+        const float4* src = reinterpret_cast<const float4*>(Wc + static_cast<size_t>(t0 + t) * R * kPanelCols);
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const int r = warp + q * kConsWarps;
+          if (r < R) {  // the same for every lane of the warp
+            const float4 v = src[r * (kPanelCols / 4) + lane];
+            __syncwarp();
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             tmem_w + static_cast<uint32_t>(4 * (RPW * t + q))),
+                         "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                         "r"(__float_as_uint(v.w))
+                         : "memory");
+          }
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+  }
 
   // ------------------------------------------------------------ producer
   if constexpr (kRowMajorW) {
@@ -1031,12 +1125,13 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
       // rest from HBM (evict_first), so that part is not re-read from DRAM
       const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
       const bool all_keep = a.resident || a.l2_keep;
+      // streamed panels only: [t0, t0 + Pt) are in tensor memory (kTmemW)
       const long long total =
-          a.resident ? a.P : static_cast<long long>(a.P) * a.rk_stages * a.S * a.T;
+          a.resident ? a.P : static_cast<long long>(Ps) * a.rk_stages * a.S * a.T;
       long long it = 0;
       int slot = 0, j = 0;
       uint32_t lap = 0;  // it / ns
-      uint32_t odd = 0;  // (it / P) & 1: the stage walks its row block backwards
+      uint32_t odd = 0;  // (it / Ps) & 1: the stage walks its row block backwards
       bool ok = true;
       for (; it < total; ++it) {
         if (!a.resident && lap > 0) {
@@ -1048,11 +1143,12 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
         mbar_arrive_expect_tx(&full[slot], panel_bytes);
         // odd stages walk the row block backwards: the panels read last in
         // one stage, still in L2, are the first the next stage needs
-        const int jp = (a.zigzag && !a.resident && odd) ? a.P - 1 - j : j;
+        int jp = (a.zigzag && !a.resident && odd) ? Ps - 1 - j : j;
+        if constexpr (kTmemW) jp += jp >= t0 ? Pt : 0;  // step over the held panels
         bulk_g2s(ring + static_cast<size_t>(slot) * slot_floats,
                  Wc + static_cast<size_t>(jp) * R * kPanelCols, panel_bytes, &full[slot],
                  (all_keep || jp < a.keep_panels) ? keep : stream);
-        if (++j == a.P) {
+        if (++j == Ps) {
           j = 0;
           odd ^= 1u;
         }
@@ -1324,6 +1420,14 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
       }
     } else {
       for (int j = 0; j < a.P; ++j) {
+        if constexpr (kTmemW) {
+          // the order of the panels is the same; those past Ps come from tensor memory
+          const int jp = (a.zigzag && (g & 1)) ? a.P - 1 - j : j;
+          if (jp >= t0 && jp < t0 + Pt) {
+            sums.panel_tmem(tmem_w + static_cast<uint32_t>(4 * RPW * (jp - t0)), xs, jp, warp, lane, R);
+            continue;
+          }
+        }
         const int slot = cslot;
         // every lane waits; the vote keeps the warp's decision uniform
         const bool landed = mbar_wait_bounded(&full[slot], cphase, a.timeout_ns, s_abort);
@@ -1375,11 +1479,26 @@ __device__ __forceinline__ void stepper_engine(const KArgs& a, const int c, cons
     ++tag;
   }
   if (!aborted && owner) prog.finish(a, node);
+  if constexpr (kTmemW) {
+    // every consumer's tensor-memory loads are done before the columns go back
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    consumer_sync_or(false);
+    if (warp == 0) {
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem),
+                   "r"(static_cast<uint32_t>(kTmemAllocCols))
+                   : "memory");
+    }
+  }
 }
 
-template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32, bool kRegW = false>
+template <int RPW, bool kRowMajorW, int kProg = kProgForward, int kW = kWf32, bool kRegW = false,
+          bool kTmemW = false>
 __global__ void __launch_bounds__(kThreads, 1) sto_persistent_kernel(const __grid_constant__ KArgs a) {
-  stepper_engine<RPW, kRowMajorW, kProg, kW, kRegW>(a, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+  stepper_engine<RPW, kRowMajorW, kProg, kW, kRegW, kTmemW>(a, static_cast<int>(blockIdx.x),
+                                                            static_cast<int>(gridDim.x));
 }
 
 // Several reservoirs with their own W in one cooperative launch.  The grid

@@ -48,7 +48,7 @@ class sto_params(ctypes.Structure):
 
 class sto_config(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("l2_keep_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("l2_keep_mb", ctypes.c_int32), ("tmem_w", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class sto_batch_plan(ctypes.Structure):
@@ -67,7 +67,8 @@ class sto_info(ctypes.Structure):
                 ("panel_cols", ctypes.c_int32), ("panels", ctypes.c_int32),
                 ("ring_slots", ctypes.c_int32), ("resident", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("sm_count", ctypes.c_int32),
-                ("w_bytes", ctypes.c_int64), ("xbuf_timed", ctypes.c_int32), ("xbuf_slot", ctypes.c_int32)]
+                ("w_bytes", ctypes.c_int64), ("xbuf_timed", ctypes.c_int32), ("xbuf_slot", ctypes.c_int32),
+                ("tmem_panels", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -228,7 +229,7 @@ def _stream_ptr(stream):
 
 
 def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout_ms=0,
-               l2_keep_mb=0):
+               l2_keep_mb=0, tmem_w=0):
     """Returns an opaque handle (int).  W, w_in, m0: numpy or torch float32."""
     lib = load_library()
     pW, kW = _ptr(W, np.float32)
@@ -236,8 +237,8 @@ def sto_create(N, params: Params, W, w_in, m0=None, stream=None, grid=0, timeout
     pm0, km0 = _ptr(m0, np.float32)
     h = _VP()
     cp = params.to_c()
-    if grid or timeout_ms or l2_keep_mb:
-        cfg = sto_config(grid=grid, timeout_ms=timeout_ms, l2_keep_mb=l2_keep_mb)
+    if grid or timeout_ms or l2_keep_mb or tmem_w:
+        cfg = sto_config(grid=grid, timeout_ms=timeout_ms, l2_keep_mb=l2_keep_mb, tmem_w=tmem_w)
         rc = lib.sto_create_ex(N, ctypes.byref(cp), pW, pwin, pm0, _stream_ptr(stream),
                                ctypes.byref(cfg), ctypes.byref(h))
     else:
@@ -563,10 +564,13 @@ class Reservoir:
 
     coupling: "f32" (FP32 W and products, W and m0 float32), or the FP64
     coupling of the paper's benchmark, "df64" (double-float products) or
-    "f64" (FP64 FMA), with W and m0 float64."""
+    "f64" (FP64 FMA), with W and m0 float64.  tmem_w: -1 streams every panel
+    of a streamed FP32 W instead of keeping the last ones in tensor memory
+    (sto_config.tmem_w; same bits)."""
 
     def __init__(self, W, w_in, params: Params | None = None, m0=None, stream=None,
-                 grid: int = 0, timeout_ms: int = 0, l2_keep_mb: int = 0, coupling: str = "f32"):
+                 grid: int = 0, timeout_ms: int = 0, l2_keep_mb: int = 0, coupling: str = "f32",
+                 tmem_w: int = 0):
         self.params = params or Params()
         self.N = int(W.shape[0])
         self.handle = None
@@ -575,7 +579,7 @@ class Reservoir:
         self.coupling = coupling
         if COUPLINGS[coupling] is None:
             self.handle = sto_create(self.N, self.params, W, w_in, m0, stream, grid, timeout_ms,
-                                     l2_keep_mb)
+                                     l2_keep_mb, tmem_w)
         else:
             self.handle = sto_create_f64(self.N, self.params, W, w_in, m0, stream, COUPLINGS[coupling],
                                          grid, timeout_ms, l2_keep_mb)

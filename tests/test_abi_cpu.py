@@ -44,7 +44,7 @@ def test_exports_are_only_the_abi():
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.sto_abi_version() == 3
+    assert lib.sto_abi_version() == 4
     for code in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
         assert sto.sto_strerror(code)
     assert "invalid" in sto.sto_strerror(-1)

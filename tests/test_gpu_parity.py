@@ -140,6 +140,34 @@ def test_streamed_ring_plan_small_grid():
     assert np.max(np.abs(st_gpu - st_orc)) <= 1e-5
 
 
+@pytest.mark.parametrize("N,grid", [(10000, 0), (6000, 148), (15000, 0), (7000, 100)])
+def test_tensor_memory_panels_give_the_same_bits(N, grid):
+    """Streamed FP32 W keeps the last panels of each row block in the SM's
+    tensor memory for the whole launch (the default); streaming every panel
+    instead (tmem_w = -1) must give the same bits, since the FP32 row sums run
+    over the same panels in the same order.  Rows per warp 5 (6 panels held),
+    3 (the 4-row form, 8 panels), 7 (the 8-row form, 4 panels), and a forced
+    grid of 100 CTAs."""
+    sto = sto_mod()
+    W, w_in, m0, u = make_system(N, "gauss", seed=N + grid, T=1)
+    P = Params(substeps=3, A_cp=50.0)
+    dev = torch.device("cuda")
+    Wt, wt, mt = (torch.from_numpy(a).to(dev) for a in (W, w_in, m0))
+    ut = torch.from_numpy(u).to(dev)
+    outs = []
+    for tmem_w in (0, -1):
+        st = torch.zeros((1, N), dtype=torch.float32, device=dev)
+        with sto.Reservoir(Wt, wt, P, m0=mt, stream=torch.cuda.current_stream(), grid=grid,
+                           tmem_w=tmem_w) as r:
+            info = r.info()
+            assert info["resident"] == 0
+            assert (info["tmem_panels"] > 0) == (tmem_w == 0)
+            r.run(ut, st)
+            outs.append((st.cpu().numpy(), r.state()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_full_size_n10000_launch_config():
     """N = 10^4 (400 MB FP32 W) in the automatic plan the benchmark times:
     one input sample of 2 RK4 steps, every output compared."""
