@@ -349,6 +349,36 @@ def test_device_timeout_is_reported_and_recoverable():
     assert np.max(np.abs(st - st_orc)) <= 1e-5
 
 
+def test_device_timeout_with_tensor_memory_panels_is_recoverable():
+    """The same stall with W streamed and panels held in tensor memory
+    (N = 10^4): every CTA's wait expires, the call returns STO_ETIMEOUT, and
+    each CTA still frees its tensor memory on the way out.  The same handle
+    then runs normally and gives the bits of a fresh handle."""
+    sto = sto_mod()
+    N = 10000
+    W, w_in, m0, u = make_system(N, "gauss", seed=12, T=2)
+    P = Params(substeps=2, A_cp=50.0)
+    dev = torch.device("cuda")
+    Wt, wt, mt, ut = (torch.from_numpy(a).to(dev) for a in (W, w_in, m0, u))
+    s = torch.cuda.current_stream()
+    st = torch.zeros((2, N), dtype=torch.float32, device=dev)
+    ref = torch.zeros((2, N), dtype=torch.float32, device=dev)
+    with sto.Reservoir(Wt, wt, P, m0=mt, stream=s, timeout_ms=100) as r:
+        assert r.info()["tmem_panels"] > 0
+        sto.sto_debug_inject_stall(r.handle, 1)
+        with pytest.raises(sto.StoError) as e:
+            r.run(ut, st)
+        assert e.value.code == sto.STO_ETIMEOUT
+        r.set_state(m0)
+        r.run(ut, st)
+        m = r.state()
+    with sto.Reservoir(Wt, wt, P, m0=mt, stream=s) as r2:
+        r2.run(ut, ref)
+        m_ref = r2.state()
+    assert np.array_equal(st.cpu().numpy(), ref.cpu().numpy())
+    assert np.array_equal(m, m_ref)
+
+
 @pytest.mark.parametrize("N", [1000, 1344, 333])
 def test_register_resident_w_plan(N):
     """N <= 1344 with at most 16 oscillators per CTA holds W in registers (the
