@@ -598,8 +598,9 @@ def time_fp64(args, seed, torch, sto, dev, hbm_peak):
             "cases": out}
 
 
-def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
-    """Node-updates/s of the FP64 oracle on a bounded sample of the workload."""
+def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads, steps=None):
+    """Node-updates/s of the FP64 oracle on a bounded sample of the workload
+    (steps RK4 steps, or as many as fit the time budget)."""
     import oracle
     W, w_in, m0, u = workload(N, 1, seed)
     W64 = W.astype(np.float64)
@@ -609,7 +610,8 @@ def cpu_oracle_rate(N, substeps_total_budget_s, seed, nthreads):
     t0 = time.perf_counter()
     m, _ = oracle.run(P, W64, w_in.astype(np.float64), m, u.astype(np.float64), nthreads=nthreads)
     one = time.perf_counter() - t0
-    steps = max(1, int(substeps_total_budget_s / max(one, 1e-6)))
+    if steps is None:
+        steps = max(1, int(substeps_total_budget_s / max(one, 1e-6)))
     t0 = time.perf_counter()
     uu = np.repeat(u.astype(np.float64), steps, axis=0)
     m, _ = oracle.run(P, W64, w_in.astype(np.float64), m, uu, nthreads=nthreads)
@@ -846,6 +848,15 @@ def main():
             "plan": small["info"], "clocks": small["clocks"],
             "e2e_value": (small["node_updates"] / small["e2e_s"]) if small.get("e2e_s") else None,
         }
+        if not args.no_cpu:
+            # the FP64 oracle at this size too, on all host cores (a bounded sample)
+            try:
+                c3 = cpu_oracle_rate(Ns, 0.0, 0, os.cpu_count() or 1, steps=2000)
+                line["also"]["cpu_oracle"] = {"value": c3["value"], "unit": "node-updates/s", "cores": c3["cores"],
+                                              "sample": f"{c3['steps']} RK4 steps of the N={Ns} workload "
+                                                        f"in {c3['seconds']:.1f} s"}
+            except Exception as e:  # informative, never fatal
+                line["also"]["cpu_oracle"] = {"error": str(e)}
     if adj is not None:
         line["adjoint"] = adj
     if sweep is not None:
