@@ -109,12 +109,13 @@ typedef struct sto_config {
   int32_t timeout_ms;  /* limit of every device-side wait (default 2000) */
   int32_t l2_keep_mb;  /* W larger than L2: MB of W kept L2-resident across
                           stages (0 = default, 110 MB; -1 = none) */
-  int32_t tmem_w;      /* FP32 W larger than L2: 0 (default) keeps the last
+  int32_t tmem_w;      /* FP32 W larger than L2: 0 (default) keeps a few
                           panels of each CTA's rows of W in the SM's tensor
                           memory for the whole call (up to 128 columns per
-                          consumer warp: 6 panels of 68 x 128 at N = 10^4),
-                          so they are not streamed again; -1 streams every
-                          panel.  The results are the same bits. */
+                          consumer warp: 6 panels of 68 x 128 at N = 10^4,
+                          from the middle of the streamed ones), so they are
+                          not streamed again; -1 streams every panel.  The
+                          results are the same bits. */
   int32_t reserved[4]; /* must be 0 */
 } sto_config;
 

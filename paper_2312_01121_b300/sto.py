@@ -565,7 +565,7 @@ class Reservoir:
     coupling: "f32" (FP32 W and products, W and m0 float32), or the FP64
     coupling of the paper's benchmark, "df64" (double-float products) or
     "f64" (FP64 FMA), with W and m0 float64.  tmem_w: -1 streams every panel
-    of a streamed FP32 W instead of keeping the last ones in tensor memory
+    of a streamed FP32 W instead of keeping a few in tensor memory
     (sto_config.tmem_w; same bits)."""
 
     def __init__(self, W, w_in, params: Params | None = None, m0=None, stream=None,
