@@ -326,7 +326,8 @@ def time_adjoint(args, seed, torch, sto, dev):
     return {"N": N, "input_samples": T, "ckpt_every": K, "ms_per_call": ms,
             "value": N * T * args.substeps / (ms / 1e3), "unit": "node-updates/s",
             "note": "gradients of a loss on the sampled states w.r.t. A_cp, I, w_in, m0; "
-                    "one call = checkpoint pass + recomputation with recording + reverse pass"}
+                    "one call = checkpoint pass, then per segment the recomputation with recording "
+                    "(beside the reverse pass of the segment after it) and the reverse pass"}
 
 
 def time_sweep(args, seed, torch, sto, dev, peaks):

@@ -254,8 +254,13 @@ typedef struct sto_grads {
  *   ckpt_every    K >= 1: the state is checkpointed every K input samples;
  *                 each K-sample segment is recomputed once with its
  *                 trajectory recorded (K * substeps * N * 40 bytes of device
- *                 memory), then swept backwards.  Cost: about three forward
- *                 runs plus one reverse run with a W^T product per stage.
+ *                 memory), then swept backwards.  Cost: two forward runs
+ *                 (the checkpoint pass, then the recomputation with
+ *                 recording) and one reverse run with a W^T product per
+ *                 stage.  With W on chip and several segments, each
+ *                 segment's recomputation runs on a second stream beside
+ *                 the reverse pass of the segment after it (another
+ *                 recording buffer of the same size; the same results).
  *   out           receives dA_cp and dcurrent; dw_in / dm0 are written if
  *                 non-NULL.
  * The state ends where sto_run would leave it.  The first call builds a

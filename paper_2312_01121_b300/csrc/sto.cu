@@ -139,6 +139,14 @@ struct sto_handle {
   double* d_gacc = nullptr;    // g_acp (N) | g_cur (N) | g_win (N n_in)
   float* d_dl = nullptr;       // staged dL/dstates
   size_t d_dl_cap = 0;
+  // the recomputation that overlaps the reverse pass (adjoint_overlap_ready)
+  float* d_rec2 = nullptr;     // a second segment recording
+  size_t d_rec2_cap = 0;
+  double* d_state2 = nullptr;  // 3N: its state
+  int* d_err2 = nullptr;       // its error word
+  int* h_err2 = nullptr;       // pinned
+  cudaStream_t s_aux = nullptr;
+  cudaEvent_t ev_aux[5] = {};  // start, recorded[2], reversed[2]
 };
 
 namespace {
@@ -158,6 +166,13 @@ void free_handle(sto_handle* h) {
   cudaFree(h->d_lam);
   cudaFree(h->d_gacc);
   cudaFree(h->d_dl);
+  cudaFree(h->d_rec2);
+  cudaFree(h->d_state2);
+  cudaFree(h->d_err2);
+  if (h->h_err2) cudaFreeHost(h->h_err2);
+  for (cudaEvent_t e : h->ev_aux)
+    if (e) cudaEventDestroy(e);
+  if (h->s_aux) cudaStreamDestroy(h->s_aux);
   if (h->h_err) cudaFreeHost(h->h_err);
   delete h;
 }
@@ -1019,6 +1034,112 @@ int sto_run(sto_handle* h, const float* u, int64_t T, float* states_out) {
   return finish_launch(h);
 }
 
+// The working set of the overlapped reverse sweep: a second recording, a
+// state copy, an error word, a stream and events.  It needs a second
+// exchange buffer, which only plans with W on chip have (the placement
+// pool); otherwise, or without the memory, the sweep runs in sequence.
+int adjoint_overlap_ready(sto_handle* h, size_t rec_floats) {
+  if (h->xbuf_n < 2) return STO_ENOTSUP;
+  if (const int rc = grow(&h->d_rec2, &h->d_rec2_cap, rec_floats)) return rc;
+  const size_t n3 = 3 * static_cast<size_t>(h->N);
+  auto fail = [&]() {
+    cudaGetLastError();
+    return STO_ENOMEM;
+  };
+  if (!h->d_state2 && cudaMalloc(&h->d_state2, n3 * 8) != cudaSuccess) return fail();
+  if (!h->d_err2 && cudaMalloc(&h->d_err2, 16) != cudaSuccess) return fail();
+  if (!h->h_err2 && cudaMallocHost(&h->h_err2, 16) != cudaSuccess) return fail();
+  if (!h->s_aux && cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) != cudaSuccess) return fail();
+  for (cudaEvent_t& e : h->ev_aux)
+    if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail();
+  return STO_OK;
+}
+
+// Step 2 of sto_adjoint with the recomputation of segment g - 1 running
+// beside the reverse pass of segment g: the recomputation on the auxiliary
+// stream (its own state copy, exchange buffer and error word, the two
+// recordings alternating), the reverse passes in order on the handle's
+// stream.  Each reverse pass waits for its segment's recording; each
+// recomputation waits for the reverse pass that last read its buffer.  The
+// launches, their inputs and their order per buffer are those of the plain
+// sweep, so the gradients are the same bits.  Both streams are idle on
+// return.
+int adjoint_reverse_overlapped(sto_handle* h, const float* d_u, const float* d_dl, int64_t K, int64_t nseg,
+                               int64_t T) {
+  cudaStream_t s = h->stream, s2 = h->s_aux;
+  const int64_t N = h->N;
+  const int n_in = h->params.n_in;
+  const size_t n3 = 3 * static_cast<size_t>(N);
+  const size_t rec_m_floats = static_cast<size_t>(K) * h->params.substeps * static_cast<size_t>(N) * 6;
+  float* recs[2] = {h->d_rec, h->d_rec2};
+  unsigned long long* xbuf2 =
+      h->d_xbuf_pool + static_cast<size_t>((h->xbuf_slot + 1) % h->xbuf_n) * (h->xbuf_stride / sizeof(unsigned long long));
+  cudaEvent_t ev_start = h->ev_aux[0];
+  cudaEvent_t* ev_rec = h->ev_aux + 1;  // recording of buffer b done
+  cudaEvent_t* ev_rev = h->ev_aux + 3;  // reverse pass over buffer b done
+  // the error words collect the first error of any launch (read at the end)
+  STO_CUDA(cudaMemsetAsync(h->d_err, 0, 16, s));
+  STO_CUDA(cudaEventRecord(ev_start, s));  // checkpoints and accumulator resets are in place
+  STO_CUDA(cudaStreamWaitEvent(s2, ev_start, 0));
+  STO_CUDA(cudaMemsetAsync(h->d_err2, 0, 16, s2));
+  auto recompute = [&](int64_t g) -> int {
+    const int b = static_cast<int>(g & 1);
+    const int64_t t0 = g * K, Tg = (T - t0) < K ? (T - t0) : K;
+    STO_CUDA(cudaMemcpyAsync(h->d_state2, h->d_ckpt + g * n3, n3 * 8, cudaMemcpyDeviceToDevice, s2));
+    sto::KArgs a = base_args(h, d_u + t0 * n_in, Tg);
+    a.state = h->d_state2;
+    a.xbuf = xbuf2;
+    a.err = h->d_err2;
+    a.inject_cta = -1;
+    a.rec_m = reinterpret_cast<float2*>(recs[b]);
+    a.rec_h = recs[b] + rec_m_floats;
+    STO_CUDA(launch_stepper(h->plan, a, s2, h->wmode));
+    STO_CUDA(cudaEventRecord(ev_rec[b], s2));
+    return STO_OK;
+  };
+  auto reverse = [&](int64_t g) -> int {
+    const int b = static_cast<int>(g & 1);
+    const int64_t t0 = g * K, Tg = (T - t0) < K ? (T - t0) : K;
+    STO_CUDA(cudaStreamWaitEvent(s, ev_rec[b], 0));
+    sto::KArgs a = base_args(h, d_u + t0 * n_in, Tg);
+    a.W = h->d_WT;
+    a.rec_m = reinterpret_cast<float2*>(recs[b]);
+    a.rec_h = recs[b] + rec_m_floats;
+    a.dLds = d_dl + t0 * N;
+    a.lam = h->d_lam;
+    a.g_acp = h->d_gacc;
+    a.g_cur = h->d_gacc + N;
+    a.g_win = h->d_gacc + 2 * N;
+    a.inject_cta = -1;
+    STO_CUDA(launch_adjoint(h->plan, a, s));
+    STO_CUDA(cudaEventRecord(ev_rev[b], s));
+    return STO_OK;
+  };
+  int rc = recompute(nseg - 1);
+  for (int64_t g = nseg - 1; g >= 0 && rc == STO_OK; --g) {
+    rc = reverse(g);
+    if (rc == STO_OK && g > 0) {
+      // buffer (g - 1) & 1 was last read by the reverse pass of g + 1
+      if (g + 1 <= nseg - 1) {
+        const cudaError_t e = cudaStreamWaitEvent(s2, ev_rev[(g - 1) & 1], 0);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+      }
+      if (rc == STO_OK) rc = recompute(g - 1);
+    }
+  }
+  // never return with work in flight on either stream
+  const cudaError_t e1 = cudaMemcpyAsync(h->h_err2, h->d_err2, 16, cudaMemcpyDeviceToHost, s2);
+  const cudaError_t e2 = cudaMemcpyAsync(h->h_err, h->d_err, 16, cudaMemcpyDeviceToHost, s);
+  const cudaError_t e3 = cudaStreamSynchronize(s2);
+  const cudaError_t e4 = cudaStreamSynchronize(s);
+  if (rc) return rc;
+  for (cudaError_t e : {e1, e2, e3, e4})
+    if (e != cudaSuccess) return cuda_fail(e);
+  for (const int* w : {h->h_err, h->h_err2})
+    if (w[0] != 0) return w[0] == sto::kErrTimeout ? STO_ETIMEOUT : STO_ECUDA;
+  return STO_OK;
+}
+
 int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstates,
                 int32_t ckpt_every, sto_grads* out) {
   if (!h || T < 1 || !u || !dL_dstates || !out || ckpt_every < 1) return STO_EINVAL;
@@ -1070,6 +1191,13 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
   float2* rec_m = reinterpret_cast<float2*>(h->d_rec);
   float* rec_h = h->d_rec + static_cast<size_t>(K) * P.substeps * N * 6;
 
+  // the tags of the whole call (three sweeps) fit before the counter wraps:
+  // a wrap resets the whole pool, which must not happen while the
+  // overlapped sweep's second exchange buffer is in use
+  if (h->stage_counter + 3 * stages + 8 * static_cast<uint64_t>(nseg) + 16 >= 0xfffffff0ULL) {
+    STO_CUDA(cudaMemsetAsync(h->d_xbuf_pool, 0xff, h->xbuf_n * h->xbuf_stride, s));
+    h->stage_counter = 0;
+  }
   // 1. checkpoints every K samples
   STO_CUDA(cudaMemcpyAsync(h->d_ckpt, h->d_state, n3 * 8, cudaMemcpyDeviceToDevice, s));
   for (int64_t g = 0; g < nseg; ++g) {
@@ -1083,6 +1211,11 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
   // 2. segments in reverse: recompute with recording, then the adjoint pass
   STO_CUDA(cudaMemsetAsync(h->d_lam, 0, n3 * 8, s));
   STO_CUDA(cudaMemsetAsync(h->d_gacc, 0, (2 + static_cast<size_t>(n_in)) * N * 8, s));
+  if (nseg > 1 && adjoint_overlap_ready(h, rec_floats) == STO_OK) {
+    // the recomputation of segment g - 1 overlaps the reverse pass of g
+    rc = adjoint_reverse_overlapped(h, d_u, d_dl, K, nseg, T);
+    if (rc) return rc;
+  } else {
   for (int64_t g = nseg - 1; g >= 0; --g) {
     const int64_t t0 = g * K, Tg = (T - t0) < K ? (T - t0) : K;
     STO_CUDA(cudaMemcpyAsync(h->d_state, h->d_ckpt + g * n3, n3 * 8, cudaMemcpyDeviceToDevice, s));
@@ -1091,6 +1224,7 @@ int sto_adjoint(sto_handle* h, const float* u, int64_t T, const float* dL_dstate
     if (!rc) rc = engine_launch_adjoint(h, d_u + t0 * n_in, Tg, d_dl + t0 * N, rec_m, rec_h);
     if (!rc) rc = finish_launch(h);
     if (rc) return rc;
+  }
   }
   // 3. results; the state ends where sto_run would leave it
   STO_CUDA(cudaMemcpyAsync(h->d_state, h->d_ckpt + nseg * n3, n3 * 8, cudaMemcpyDeviceToDevice, s));

@@ -63,6 +63,28 @@ def test_checkpoint_interval_does_not_change_gradients(sto):
         assert abs(g["current"] - out[0]["current"]) <= 1e-9 * abs(out[0]["current"])
 
 
+def test_overlapped_reverse_sweep_gives_the_sequential_bits(sto):
+    """N = 1000 (W on chip, 63 CTAs, a pool of exchange-buffer placements):
+    with several checkpoint segments the recomputation of segment g - 1 runs
+    on a second stream beside the reverse pass of segment g; with one
+    segment the sweep is sequential.  The checkpoint interval changes no
+    arithmetic (test above), so every interval gives the same gradients."""
+    N, T = 1000, 8
+    W, w_in, m0, u = make_system(N, "gauss", seed=6, T=T)
+    P = sto.Params(substeps=10, A_cp=50.0)
+    G = np.random.default_rng(2).standard_normal((T, N)).astype(np.float32)
+    out = []
+    for K in (8, 1, 2, 3):  # 8: one segment, in sequence; the others overlapped
+        with sto.Reservoir(W, w_in, P, m0=m0) as r:
+            assert r.info()["grid"] > 1 and r.info()["resident"] == 1
+            out.append((r.adjoint(u, G, ckpt_every=K), r.state()))
+    for g, m in out[1:]:
+        assert np.array_equal(m, out[0][1])
+        assert np.array_equal(g["m0"], out[0][0]["m0"]) and np.array_equal(g["w_in"], out[0][0]["w_in"])
+        assert abs(g["A_cp"] - out[0][0]["A_cp"]) <= 1e-9 * abs(out[0][0]["A_cp"])
+        assert abs(g["current"] - out[0][0]["current"]) <= 1e-9 * abs(out[0][0]["current"])
+
+
 def test_adjoint_matches_finite_differences_n1000(sto):
     """N = 1000, A_cp = 300: L = G . m^x after the last sample.
     (a) central differences (h = 1e-4 relative) of the FP64 oracle's forward;
