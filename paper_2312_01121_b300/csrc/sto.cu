@@ -2111,27 +2111,40 @@ int sto_batch_create(int64_t N, int32_t R, const sto_params* params, const doubl
   if ((e = cudaMemcpyAsync(b->hs0, hs0.data(), R * sizeof(sto::df), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->aing, aing.data(), R * sizeof(sto::df), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return fail(cuda_fail(e));
-  // states: mn = ms = m0, ksum = 0  (device layout [3][R][N] df)
-  std::vector<float2> st(9 * RN, make_float2(0.f, 0.f));
-  std::vector<float> mf;
-  if (m0) {
-    rc = fetch_floats(&mf, m0, 3 * RN, s);
-    if (rc) return fail(rc);
-  }
+  // states: mn = ms = m0, ksum = 0 (device layout [3][R][N] df), formed on
+  // the device: at R N = 2^29 the state is 38.6 GB, more than a host copy
+  // should ever hold
   const double phi0 = 2.0 * M_PI / 360.0;
   const double ic[3] = {std::sin(phi0) * std::cos(phi0), std::sin(phi0) * std::sin(phi0), std::cos(phi0)};
-  for (int r = 0; r < R; ++r)
-    for (int i = 0; i < 3; ++i)
-      for (int64_t k = 0; k < N; ++k) {
-        const double v = m0 ? mf[(static_cast<size_t>(r) * 3 + i) * N + k] : ic[i];
-        if (!std::isfinite(v)) return fail(STO_ENONFINITE);
-        const sto::df d = sto::df_split_host(v);
-        st[i * RN + static_cast<size_t>(r) * N + k] = make_float2(d.hi, d.lo);
-        st[3 * RN + i * RN + static_cast<size_t>(r) * N + k] = make_float2(d.hi, d.lo);
+  const float* d_m0 = nullptr;
+  float* m0_tmp = nullptr;
+  if (m0) {
+    if (is_device_ptr(m0)) {
+      d_m0 = m0;
+    } else {
+      if (cudaMalloc(reinterpret_cast<void**>(&m0_tmp), 3 * RN * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STO_ENOMEM);
       }
-  if ((e = cudaMemcpyAsync(b->st, st.data(), st.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess)
-    return fail(cuda_fail(e));
+      if ((e = cudaMemcpyAsync(m0_tmp, m0, 3 * RN * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        cudaFree(m0_tmp);
+        return fail(cuda_fail(e));
+      }
+      d_m0 = m0_tmp;
+    }
+  }
+  e = cudaMemsetAsync(b->d_err, 0, 16, s);
+  if (e == cudaSuccess) {
+    const long long total = 3LL * static_cast<long long>(RN);
+    const unsigned blocks = static_cast<unsigned>(total / 256 + 1 < 65536 ? total / 256 + 1 : 65536);
+    sto::sweep_state_init_kernel<<<blocks, 256, 0, s>>>(d_m0, R, N, ic[0], ic[1], ic[2], b->st, b->d_err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(m0_tmp);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  if (b->h_err[0] != 0) return fail(STO_ENONFINITE);
   // the launch plan (tile width, ring depth) is chosen by the first run
   // (autotuner) or by sto_batch_set_plan
   *out = b;

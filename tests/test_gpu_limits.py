@@ -91,3 +91,38 @@ def test_largest_fp64_reservoir(sto, coupling):
     with pytest.raises(sto.StoError) as e:
         sto.Reservoir(Z, np.zeros((N + 1, 1), np.float32), P, coupling=coupling)
     assert e.value.code == sto.STO_ENOTSUP
+
+
+def test_largest_sweep(sto):
+    """R N = 2^29 (R = 32768 reservoirs sharing one N = 16384 W), the largest
+    batch the sweep's 32-bit per-pair offsets allow: its state is 38.6 GB,
+    formed on the device.  One RK4 step with BN = 40 (a ragged last tile of
+    8 reservoirs); three sampled reservoirs against the oracle on the
+    BF16-rounded W (1e-5).  One reservoir more is refused."""
+    N, R = 16384, 32768
+    W, w_in, _, u = make_system(N, "gauss", seed=23, T=1)
+    rng = np.random.default_rng(23)
+    cur = rng.uniform(1e-3, 3e-3, R)
+    gain = rng.uniform(0.5, 2.0, R)
+    P = sto.Params(substeps=1, A_cp=50.0, A_in=20.0)
+    dev = torch.device("cuda")
+    st = torch.zeros((1, R, N), dtype=torch.float32, device=dev)
+    sw = sto.Sweep(W, w_in, P, currents=cur, gains=gain)
+    try:
+        sw.set_plan(40, 3, 2, 1, 512)
+        sw.run(u, st)
+        picks = (0, R // 2 - 1, R - 1)
+        got = {r: st[0, r].cpu().numpy() for r in picks}
+    finally:
+        sw.close()
+    del st
+    Wb = torch.from_numpy(W).to(torch.bfloat16).float().numpy().astype(np.float64)
+    m0 = np.asarray(oracle.initial_state(N), np.float64)
+    for r in picks:
+        OP = oracle_params(P.replace(current=float(cur[r]), input_gain=float(gain[r])))
+        _, ref = oracle.run(OP, Wb, w_in.astype(np.float64), m0, u.astype(np.float64), nthreads=NTHREADS)
+        assert np.max(np.abs(got[r] - ref[0])) <= 1e-5, r
+    del Wb
+    with pytest.raises(sto.StoError) as e:
+        sto.Sweep(W, w_in, P, currents=np.full(R + 1, 2e-3))
+    assert e.value.code == sto.STO_ENOTSUP

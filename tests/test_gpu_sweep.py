@@ -482,3 +482,30 @@ def test_whole_sweep_configuration_in_one_launch(sto):
         assert np.max(np.abs(st_g[i] - ref)) <= 1e-5, i
     for obj in [grp, sw] + res:
         obj.close()
+
+
+def test_sweep_initial_state_from_device_or_host_and_nonfinite(sto):
+    """The batch's initial state is formed on the device from m0 ([R][3][N]
+    float32): a device m0 gives the same state as the same host m0, the
+    default is Eq. (initial) for every oscillator, and a NaN anywhere in m0
+    is refused with STO_ENONFINITE."""
+    N, R = 130, 7
+    W, w_in, _, u = make_system(N, "gauss", seed=41, T=1)
+    m0 = np.stack([make_system(N, "gauss", seed=141 + r, T=1)[2] for r in range(R)]).astype(np.float32)
+    P = sto.Params(substeps=2)
+    with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3), m0=m0) as a:
+        s_host = a.state()
+    with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3), m0=torch.from_numpy(m0).cuda()) as b:
+        s_dev = b.state()
+    assert np.array_equal(s_host, s_dev)
+    assert np.array_equal(s_host, m0.astype(np.float64))
+    with sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3)) as c:
+        s_ic = c.state()
+    ic = np.asarray(oracle.initial_state(N), np.float64)
+    for r in range(R):
+        assert np.max(np.abs(s_ic[r] - ic)) <= 1e-7
+    bad = m0.copy()
+    bad[3, 1, 17] = np.nan
+    with pytest.raises(sto.StoError) as e:
+        sto.Sweep(W, w_in, P, currents=np.full(R, 2e-3), m0=bad)
+    assert e.value.code == sto.STO_ENONFINITE
